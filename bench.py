@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the per-pixel Whitted ray tracer (arXiv 2305.07450) on B300.
+
+One step = one frame of the workload rendered by rt_render (all steps of the hot
+path: staging, primary rays, closest hits, shading, shadow rays, reflection
+bounces, framebuffer write) from a scene already resident in HBM.  Prints ONE
+JSON line.  Default workload: 3840x2160 RGBA8, 256 spheres + plane, 3 point + 1
+square area light (16 Philox samples), depth 8.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank renders its own frames (independent replicas, no
+collective on the data path): value = frames of all ranks / max-over-ranks time.
+--impl reference times the FP64 oracle (the CPU baseline) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2305_07450_b300 import scenes as S  # noqa: E402
+
+METRIC = "frames/s & Mrays/s at 720p/1080p/4K vs FP32 roofline; fwd+adjoint frames/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32 work per counted operation (minimal formulas, FMA = 2 flops;
+# square roots, reciprocals and exp2/log2 are MUFU work and not counted).
+FLOPS = {
+    "closest_sphere_tests": 17,   # oc (3), b' = oc.d (5), c' = oc.oc - r^2 (7), disc (2)
+    "closest_plane_tests": 12,    # d.n (5), o.n + d (6), t (1)
+    "shadow_sphere_tests": 17,
+    "shadow_plane_tests": 12,
+    "primary_rays": 20,           # NDC (4), u R + v U + b F (12), normalise (4)
+    "hits": 50,                   # point, normal, face-forward, offset, reflection, accumulate
+    "light_evals": 16,            # L - p, |L - p|^2, normalise, n.l for every light at a hit
+    "lit_lights": 21,             # Phong r, v.r, x^32, A and S updates
+    "light_samples": 18,          # sample point and its unit direction
+}
+
+
+def flops_of(c: dict) -> float:
+    return sum(FLOPS[k] * c[k] for k in FLOPS)
+
+
+def rays_of(c: dict) -> float:
+    return c["primary_rays"] + c["reflection_rays"] + c["shadow_rays"]
+
+
+def workload(name: str) -> S.Workload:
+    return S.WORKLOADS[name]()
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_sample(w: S.Workload, budget_s: float, threads: int | None = None):
+    """Time the oracle (as it stands) on a lattice sample of the frame sized to
+    roughly budget_s seconds; returns frames/s, Mrays/s, counters per pixel."""
+    import oracle
+    W, H = w.params.width, w.params.height
+    stride = max(1, int(math.sqrt(W * H / 2048)))
+    for _ in range(4):
+        px = S.pixel_lattice(W, H, stride)
+        t0 = time.perf_counter()
+        r = oracle.trace(w.scene, w.camera, w.params, px, counters=True, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * budget_s or stride == 1:
+            break
+        stride = max(1, int(stride / math.sqrt(min(budget_s / max(dt, 1e-3), 400.0))))
+    c = dict(r["counters"])
+    per_px = {k: v / len(px) for k, v in c.items()}
+    per_px["light_evals"] = per_px["hits"] * w.scene.n_lights
+    frac = len(px) / float(W * H)
+    return {
+        "frames_per_s": frac / dt,
+        "seconds": dt,
+        "pixels": int(len(px)),
+        "stride": stride,
+        "threads": int(r["threads"]),
+        "per_pixel": per_px,
+        "mrays_per_s": rays_of(c) / dt / 1e6,
+    }
+
+
+def host_cpu_name() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- traffic record
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_07450_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name: str):
+    """DRAM bytes per launch of the forward kernel from the committed ncu summary,
+    only if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 4 and not ln.startswith("#") and f[0] == "rt_fwd_kernel" and f[1] == want \
+                and f[2] == workload_name:
+            return float(f[3])
+    return None
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2305_07450_b300 import rt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    w = workload(args.workload)
+    W, H = w.params.width, w.params.height
+
+    # CPU baseline first (host threads only; no process is forked after CUDA init)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, args.cpu_budget)
+
+    ds = rt.DeviceScene(w.scene)
+    out, pitch = rt.alloc_output(w.params, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    launch = None
+
+    def step():
+        rt.render(ds, w.camera, w.params, out=out, pitch=pitch, launch=launch, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n0 = rt.launch_count()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        for a, b in evs:
+            flush.zero_()                       # L2 flush between timed frames
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    launches = rt.launch_count() - n0
+    ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = sum(ms) / len(ms)
+    total_s = sum(ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    frames = world * args.steps
+    fps = frames / total_s
+    assert rt.device_errors() == 0
+
+    # end to end through the public API with host buffers: scene records from host
+    # memory (pinned staging inside rt_scene_update), render, framebuffer to pinned host
+    host_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        ds.update(w.scene, stream=stream)
+        step()
+        host_out.copy_(out, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_fps = 1e3 / (sum(e2e_ms) / len(e2e_ms)) * world
+
+    rec = None
+    if rank == 0:
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        clocks = clk.summary()
+        rec = {
+            "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded scene (PCG64), no dataset",
+            "config": {"workload": w.name, "width": W, "height": H, "spheres": w.scene.n_spheres,
+                       "lights": w.scene.n_lights, "max_depth": w.params.max_depth,
+                       "shadow_samples": w.params.shadow_samples, "out": "rgba8" if w.params.out_format == 0 else "f32",
+                       "l2": f"flushed between timed frames ({L2_FLUSH_BYTES >> 20} MB write)",
+                       "parallelism": f"replicas x{world}", "launch": launch or "default 16x16, TMA staging"},
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        per_px = cpu["per_pixel"] if cpu else None
+        if per_px:
+            flops_frame = flops_of(per_px) * W * H
+            rays_frame = rays_of(per_px) * W * H
+            achieved = flops_frame / (ms_step / 1e3) / 1e12
+            peak_max = sm_count * 128 * 2 * 2032e6 / 1e12
+            rec["mrays_per_s"] = rays_frame * fps / 1e6
+            rec["roofline"] = {
+                "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+                "frac": achieved / peak_max,
+                "traffic": recorded_traffic(w.name),
+                "kernel": "rt_fwd_kernel",
+                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)",
+                "frac_at_measured_clock": (achieved / (sm_count * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                           if clocks.get("sm_mhz") else None),
+                "algorithmic_gflop_per_frame": flops_frame / 1e9,
+                "work_basis": f"oracle counters on a {cpu['pixels']}-pixel lattice (stride {cpu['stride']}) x W*H",
+            }
+        if cpu:
+            rec["cpu_baseline"] = {"value": cpu["frames_per_s"], "unit": "frames/s", "cores": cpu["threads"],
+                                   "kind": "oracle",
+                                   "sample": f"{cpu['pixels']} pixels (lattice stride {cpu['stride']}) of the frame, "
+                                             f"{cpu['seconds']:.1f} s, scaled to frames/s",
+                                   "cpu": host_cpu_name(), "mrays_per_s": cpu["mrays_per_s"]}
+        rec["e2e"] = {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": int(ds.nbytes),
+                      "d2h_bytes_per_step": int(out.numel() * out.element_size())}
+    ds.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return rec
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    w = workload(args.workload)
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = oracle_sample(w, args.ref_budget)
+        if i >= args.warmup:
+            vals.append(info["frames_per_s"])
+    fps = statistics.mean(vals)
+    return {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / fps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic: seeded scene (PCG64), no dataset",
+        "config": {"workload": w.name},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": info["threads"], "kind": "oracle",
+                         "sample": f"{info['pixels']} pixels (lattice stride {info['stride']}) per step, "
+                                   f"scaled to frames/s", "cpu": host_cpu_name()},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(S.WORKLOADS), default="4k")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rec = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if rec is not None:
+        print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * rt.h -- C ABI of the B300 (sm_103a) per-pixel Whitted ray tracer of
+ * "Accelerating Java Ray Tracing Applications on Heterogeneous Hardware"
+ * (arXiv 2305.07450, Section 3).
+ *
+ * The paper's accelerated method is one call, Renderer::render(pixels, dimensions,
+ * camera, rayTracingProperties, bodyPositions, bodySizes, bodyColors,
+ * bodyReflectivities, skybox, skyboxDimensions) (Section 3.9, render signature
+ * listing), fed by a task schedule that streams the camera, the properties and the
+ * body positions in every frame and streams the pixels out (Section 3.9, task
+ * schedule listing).  Here that split becomes: upload the scene once
+ * (rt_scene_upload / rt_scene_update), then render as often as wanted (rt_render);
+ * the framebuffer stays on the device.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers; every other pointer is a host
+ *    pointer that the call reads before it returns (the caller keeps ownership).
+ *  - The caller owns every output, hit-record, gradient and workspace buffer; the
+ *    library owns the memory behind an rt_scene handle.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued asynchronously on it; the call returns once it is enqueued.
+ *  - Arguments are validated on the host before any launch; an invalid argument
+ *    returns RT_ERR_INVALID_ARG and enqueues nothing.  Launch failures are mapped
+ *    from cudaGetLastError to RT_ERR_CUDA.  Nothing aborts, throws or traps.
+ *  - Waits inside kernels are bounded; a wait that gives up sets a device error
+ *    word instead of hanging, which rt_device_errors() reports.
+ *  - FP32 arithmetic on the device; all records are FP32.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,   /* a null pointer, size, format or record out of range */
+    RT_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed                 */
+    RT_ERR_OOM = 3,           /* device or pinned host allocation failed              */
+    RT_ERR_UNSUPPORTED = 4,   /* valid input outside what this build handles          */
+    RT_ERR_TIMEOUT = 5        /* a bounded device wait gave up (see rt_device_errors) */
+} rt_status;
+
+enum { RT_PHONG = 0, RT_BLINN_PHONG = 1 };          /* Section 3.5.1 / 3.5.2           */
+enum { RT_OUT_RGBA8 = 0, RT_OUT_F32 = 1 };          /* toInt of Section 3.9 / linear   */
+
+#define RT_SPHERE_FIELDS 10
+#define RT_PLANE_FIELDS 10
+#define RT_LIGHT_FIELDS 8
+#define RT_MAX_LIGHTS 16
+#define RT_MAX_SAMPLES 1024
+#define RT_MAX_DEPTH 16
+
+/* Scene records (Section 3.4 object table: position, size, colour, reflectivity;
+ * widened by the material fields the shading of Section 3.5 needs).
+ *   sphere [10]: cx, cy, cz, radius, albedo r, g, b, k_s, spec_exp, reflectivity
+ *   plane  [10]: nx, ny, nz, d (n.x + d = 0, |n| = 1), albedo r, g, b, k_s,
+ *                spec_exp, reflectivity
+ *   light  [8] : x, y, z, intensity, area_side (> 0: horizontal square light of
+ *                that side, sampled on a stratified grid), sphere_radius (> 0:
+ *                spherical light sampled with sunflower points, Section 3.6.1),
+ *                0, 0.  Both zero = point light.
+ * Reflectivity is the reflection ratio of Section 3.7 in [0, 1].  The ground plane
+ * is optional (has_plane), infinite and two-sided.  Pointers are host pointers for
+ * rt_scene_upload; for rt_scene_update they are host or device pointers as the
+ * caller states.  Lights must lie outside every sphere (RT_ERR_UNSUPPORTED
+ * otherwise): the device's shadow test relies on it. */
+typedef struct {
+    int32_t n_spheres;
+    const float *spheres;     /* [n_spheres][10] */
+    int32_t has_plane;
+    const float *plane;       /* [10], may be NULL when has_plane == 0 */
+    int32_t n_lights;         /* 0 .. RT_MAX_LIGHTS */
+    const float *lights;      /* [n_lights][8] */
+} rt_scene_desc;
+
+/* The paper's camera float[6] (Section 3.1, Section 3.9): position, yaw and pitch
+ * in degrees (pitch about x first, positive looks up; then yaw about y, positive
+ * turns toward +x), field of view in degrees spanning the shorter image side. */
+typedef struct {
+    float pos[3];
+    float yaw_deg, pitch_deg, fov_deg;
+} rt_camera;
+
+/* The paper's dimensions int[2] and rayTracingProperties int[2] (Section 3.9:
+ * shadow sample size, reflection bounce limit), plus the choices the paper leaves
+ * open. */
+typedef struct {
+    int32_t width, height;    /* 1 .. 32768 each                                      */
+    int32_t max_depth;        /* reflection bounce limit D, 0 .. RT_MAX_DEPTH          */
+    int32_t shadow_samples;   /* samples per sampled light, 1 .. RT_MAX_SAMPLES; a
+                                 perfect square when a square area light is present   */
+    int32_t shading_model;    /* RT_PHONG or RT_BLINN_PHONG                            */
+    int32_t out_format;       /* RT_OUT_RGBA8 (uint32 0xAABBGGRR) or RT_OUT_F32
+                                 (float RGBA, A = 1, linear, not clamped)             */
+    float ambient;            /* ambient strength k_a in [0, 1] (Section 3.5.1)        */
+    float eps;                /* offset of secondary ray origins along the normal     */
+    uint64_t seed;            /* Philox4x32-10 key of the area-light samples           */
+} rt_render_params;
+
+/* Launch shape of the render kernels.  A zeroed struct (or NULL) means "library
+ * default".  Threads of a CTA form block_x * block_y pixels; each warp covers an
+ * 8 x 4 pixel patch.  staging: 0 = default, 1 = one TMA bulk copy of the scene
+ * table into shared memory, 2 = cooperative copy by all threads (same results
+ * bit for bit). */
+typedef struct {
+    int32_t block_x, block_y; /* multiples of 8 and 4, block_x * block_y in 32..256 */
+    int32_t staging;
+    int32_t min_blocks_per_sm;/* occupancy hint for the batch kernel's grid size     */
+} rt_launch_config;
+
+typedef struct rt_scene rt_scene;   /* opaque, device-resident */
+
+/* Copy a scene to the device (Section 3.9: the body arrays streamed in).  Validates
+ * every record; enqueues one host-to-device copy on `stream` from a pinned staging
+ * buffer owned by the handle.  *out receives a new handle (free with rt_scene_free).
+ * Errors: RT_ERR_INVALID_ARG (null pointers, counts, non-finite or out-of-range
+ * fields), RT_ERR_UNSUPPORTED (a light inside a sphere), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_scene_upload(const rt_scene_desc *desc, void *stream, rt_scene **out);
+
+/* Overwrite the contents of a scene in place with a description of the same
+ * counts (the paper's per-frame streamIn of the body positions; also the
+ * parameter update of inverse rendering).  desc_on_device != 0: the three record
+ * pointers are device pointers, copied device-to-device without host validation.
+ * Counts must match the handle's (RT_ERR_INVALID_ARG otherwise). */
+rt_status rt_scene_update(rt_scene *scene, const rt_scene_desc *desc, int32_t desc_on_device,
+                          void *stream);
+
+/* Release a scene's device and pinned memory (synchronises the device first).
+ * NULL is accepted. */
+rt_status rt_scene_free(rt_scene *scene);
+
+/* Render one frame: for every pixel (x, y) a primary ray through its NDC point
+ * (Section 3.2, 3.3), the closest of all primitives by brute force (Section
+ * 3.4.1), ambient + per-light diffuse and specular shading with hard or sampled
+ * shadows (Sections 3.5, 3.6), reflection bounces to depth D (Section 3.7) and the
+ * colour written to the framebuffer (Section 3.9 render listing).
+ *   out_dev: device buffer of `height` rows, `out_pitch_bytes` apart (a multiple
+ *            of 16, >= width * 4 for RGBA8 or width * 16 for F32); row y holds
+ *            pixel x at byte offset x * 4 (RGBA8) or x * 16 (F32 RGBA).
+ *   hitrec_dev: NULL, or a device buffer of rt_hitrec_bytes() bytes that receives
+ *            the per-pixel hit record used by rt_render_backward.
+ *   cfg:     launch shape (NULL = default).
+ * One kernel launch on `stream`. */
+rt_status rt_render(const rt_scene *scene, const rt_camera *cam, const rt_render_params *params,
+                    void *out_dev, size_t out_pitch_bytes, void *hitrec_dev,
+                    const rt_launch_config *cfg, void *stream);
+
+/* Bytes of the hit record of one frame: for each bounce k in 0..D and each pixel,
+ * the primitive id (int32, -1 = miss), the hit distance t (float) and the visible
+ * fraction of every light (float), stored plane by plane:
+ *   element (k, f, y, x) at 4 * (((k * (2 + L) + f) * H + y) * W + x),
+ *   f = 0 id, 1 t, 2 + l visibility of light l. */
+size_t rt_hitrec_bytes(const rt_scene *scene, const rt_render_params *params);
+
+/* Bytes of the scene's device table: what rt_scene_upload and a host-side
+ * rt_scene_update copy to the device.  0 for NULL. */
+size_t rt_scene_bytes(const rt_scene *scene);
+
+/* Read and clear the device error word (bit 0: a shared-memory staging wait gave
+ * up; bit 1: a batch work-queue wait gave up).  Synchronises `stream`.  Returns
+ * RT_ERR_TIMEOUT when a bit was set, RT_OK otherwise; *bits (nullable) receives
+ * the word. */
+rt_status rt_device_errors(void *stream, uint32_t *bits);
+
+/* Number of this library's kernel launches enqueued since the process started
+ * (host-side count; used to report launches in benchmarks). */
+uint64_t rt_launch_count(void);
+
+/* Human-readable name of a status. */
+const char *rt_status_string(rt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_H */

@@ -1,0 +1,457 @@
+// rt_api.cu -- the C ABI of include/rt.h and the kernels behind it, for sm_103a.
+// One translation unit: the device error word and the kernels live here.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/rt.h"
+#include "rt_device.cuh"
+#include "rt_stage.cuh"
+#include "rt_trace.cuh"
+
+using namespace rtd;
+
+// Device error word: bits set by bounded waits that gave up (read by
+// rt_device_errors).
+static __device__ uint32_t g_err_word;
+
+static std::atomic<uint64_t> g_launches{0};
+
+struct rt_scene {
+    int ns = 0, ns_pad = 0, has_plane = 0, nl = 0;
+    int any_area = 0, any_sphere_light = 0;
+    size_t bytes = 0;
+    void* dev = nullptr;     // device blob: header, geo, mat, mat2
+    void* pinned = nullptr;  // host staging of the blob
+    cudaEvent_t copy_done = nullptr;
+    int device = 0;
+};
+
+static SceneView view_of(const rt_scene* s) {
+    const char* b = static_cast<const char*>(s->dev);
+    SceneView v;
+    v.hdr = reinterpret_cast<const SceneHdr*>(b);
+    v.geo = reinterpret_cast<const float4*>(b + sizeof(SceneHdr));
+    v.mat = v.geo + s->ns_pad;
+    v.mat2 = v.mat + s->ns_pad;
+    return v;
+}
+
+// ============================================================ forward kernel
+// One thread per pixel.  The CTA covers block_x x block_y pixels; warp w covers an
+// 8 x 4 patch (lanes 0..7 = one row), so that a warp's primary and shadow rays
+// are coherent.  The scene header and geometry table are staged in shared memory
+// once per CTA.
+template <bool HITREC>
+__global__ void __launch_bounds__(256) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
+                                                     size_t pitch, float* __restrict__ hr, size_t hr_plane,
+                                                     int staging, int block_x, int block_y) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (staging == 1 && tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const uint32_t stage_bytes = (uint32_t)(sizeof(SceneHdr) + 16u * (uint32_t)__ldg(&sv.hdr->ns_pad));
+    if (!stage_to_smem(smem, sv.hdr, stage_bytes, staging, &bar, phase, &g_err_word)) return;
+    const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
+    const StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.mat, sv.mat2};
+
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int wpr = block_x >> 3;
+    const int x = blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
+    const int y = blockIdx.y * block_y + (warp / wpr) * 4 + (lane >> 3);
+    const bool valid = x < fr.W && y < fr.H;
+    float3 c = make_float3(0.f, 0.f, 0.f);
+    if (valid) c = trace_pixel<HITREC>(sc, fr, x, y, hr, hr_plane);
+
+    if (fr.fmt == RT_OUT_F32) {
+        if (valid)
+            *reinterpret_cast<float4*>(static_cast<char*>(out) + (size_t)y * pitch + (size_t)x * 16) =
+                make_float4(c.x, c.y, c.z, 1.0f);
+    } else {
+        // four horizontally adjacent pixels (lanes 4j..4j+3) -> one 16-byte store
+        const uint32_t p0 = pack_rgba8(c);
+        const uint32_t p1 = __shfl_down_sync(0xffffffffu, p0, 1);
+        const uint32_t p2 = __shfl_down_sync(0xffffffffu, p0, 2);
+        const uint32_t p3 = __shfl_down_sync(0xffffffffu, p0, 3);
+        if ((lane & 3) == 0 && y < fr.H && x < fr.W) {
+            uint32_t* row = reinterpret_cast<uint32_t*>(static_cast<char*>(out) + (size_t)y * pitch);
+            if (x + 3 < fr.W) {
+                *reinterpret_cast<uint4*>(row + x) = make_uint4(p0, p1, p2, p3);
+            } else {
+                row[x] = p0;
+                if (x + 1 < fr.W) row[x + 1] = p1;
+                if (x + 2 < fr.W) row[x + 2] = p2;
+            }
+        }
+    }
+}
+
+// Device-side packing of scene records (rt_scene_update with device pointers):
+// thread i < ns packs sphere i; thread ns packs the header's plane and lights.
+__global__ void rt_pack_kernel(SceneView sv, int ns, const float* __restrict__ sph, int has_plane,
+                               const float* __restrict__ plane, int nl, const float* __restrict__ lights) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float4* geo = const_cast<float4*>(sv.geo);
+    float4* mat = const_cast<float4*>(sv.mat);
+    float4* mat2 = const_cast<float4*>(sv.mat2);
+    if (i < ns) {
+        const float* f = sph + 10 * (size_t)i;
+        geo[i] = make_float4(f[0], f[1], f[2], f[3] * f[3]);
+        mat[i] = make_float4(f[4], f[5], f[6], f[7]);
+        mat2[i] = make_float4(f[8], f[9], f[3], __frcp_rn(f[3]));
+    } else if (i == ns) {
+        SceneHdr* h = const_cast<SceneHdr*>(sv.hdr);
+        if (has_plane) {
+            h->plane_g = make_float4(plane[0], plane[1], plane[2], plane[3]);
+            h->plane_m = make_float4(plane[4], plane[5], plane[6], plane[7]);
+            h->plane_m2 = make_float4(plane[8], plane[9], 0.f, 0.f);
+        }
+        for (int l = 0; l < nl; ++l) {
+            const float* f = lights + 8 * l;
+            h->light_p[l] = make_float4(f[0], f[1], f[2], f[3]);
+            h->light_s[l] = make_float4(f[4], f[5], 0.f, 0.f);
+        }
+    }
+}
+
+// ============================================================ host helpers
+namespace {
+
+bool finite_all(const float* f, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(f[i])) return false;
+    return true;
+}
+
+// Distance from point c to the axis-aligned horizontal square of side a centred
+// at L (y = L.y).
+double dist_point_square(const double* c, const float* L, double a) {
+    const double h = a / 2;
+    const double dx = std::fmax(std::fabs(c[0] - L[0]) - h, 0.0);
+    const double dz = std::fmax(std::fabs(c[2] - L[2]) - h, 0.0);
+    const double dy = c[1] - L[1];
+    return std::sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+rt_status validate_desc(const rt_scene_desc* d) {
+    if (!d || d->n_spheres < 0 || d->n_spheres > (1 << 20) || d->n_lights < 0 || d->n_lights > RT_MAX_LIGHTS)
+        return RT_ERR_INVALID_ARG;
+    if ((d->n_spheres && !d->spheres) || (d->n_lights && !d->lights) || (d->has_plane && !d->plane))
+        return RT_ERR_INVALID_ARG;
+    for (int i = 0; i < d->n_spheres; ++i) {
+        const float* f = d->spheres + 10 * (size_t)i;
+        if (!finite_all(f, 10) || !(f[3] > 0.f) || f[7] < 0.f || f[8] < 0.f || f[9] < 0.f || f[9] > 1.f)
+            return RT_ERR_INVALID_ARG;
+    }
+    if (d->has_plane) {
+        const float* f = d->plane;
+        if (!finite_all(f, 10) || f[7] < 0.f || f[8] < 0.f || f[9] < 0.f || f[9] > 1.f) return RT_ERR_INVALID_ARG;
+        const double nn = (double)f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2];
+        if (std::fabs(nn - 1.0) > 1e-5) return RT_ERR_INVALID_ARG;
+    }
+    for (int l = 0; l < d->n_lights; ++l) {
+        const float* f = d->lights + 8 * l;
+        if (!finite_all(f, 8) || f[3] < 0.f || f[4] < 0.f || f[5] < 0.f || (f[4] > 0.f && f[5] > 0.f))
+            return RT_ERR_INVALID_ARG;
+        // the shadow test needs every light (its whole sampled extent) outside every sphere
+        for (int i = 0; i < d->n_spheres; ++i) {
+            const float* s = d->spheres + 10 * (size_t)i;
+            const double c[3] = {s[0], s[1], s[2]};
+            double dist;
+            if (f[4] > 0.f) {
+                dist = dist_point_square(c, f, f[4]);
+            } else {
+                const double dx = c[0] - f[0], dy = c[1] - f[1], dz = c[2] - f[2];
+                dist = std::sqrt(dx * dx + dy * dy + dz * dz) - f[5];
+            }
+            if (!(dist > (double)s[3])) return RT_ERR_UNSUPPORTED;
+        }
+    }
+    return RT_OK;
+}
+
+void pack_host(const rt_scene_desc* d, int ns_pad, unsigned char* blob) {
+    std::memset(blob, 0, scene_bytes(ns_pad));
+    SceneHdr* h = reinterpret_cast<SceneHdr*>(blob);
+    h->ns = d->n_spheres;
+    h->ns_pad = ns_pad;
+    h->has_plane = d->has_plane ? 1 : 0;
+    h->nl = d->n_lights;
+    if (d->has_plane) {
+        const float* f = d->plane;
+        h->plane_g = make_float4(f[0], f[1], f[2], f[3]);
+        h->plane_m = make_float4(f[4], f[5], f[6], f[7]);
+        h->plane_m2 = make_float4(f[8], f[9], 0.f, 0.f);
+    }
+    for (int l = 0; l < d->n_lights; ++l) {
+        const float* f = d->lights + 8 * l;
+        h->light_p[l] = make_float4(f[0], f[1], f[2], f[3]);
+        h->light_s[l] = make_float4(f[4], f[5], 0.f, 0.f);
+    }
+    float4* geo = reinterpret_cast<float4*>(blob + sizeof(SceneHdr));
+    float4* mat = geo + ns_pad;
+    float4* mat2 = mat + ns_pad;
+    for (int i = 0; i < ns_pad; ++i) {
+        if (i < d->n_spheres) {
+            const float* f = d->spheres + 10 * (size_t)i;
+            geo[i] = make_float4(f[0], f[1], f[2], (float)((double)f[3] * f[3]));
+            mat[i] = make_float4(f[4], f[5], f[6], f[7]);
+            mat2[i] = make_float4(f[8], f[9], f[3], (float)(1.0 / (double)f[3]));
+        } else {
+            geo[i] = make_float4(0.f, 0.f, 0.f, -1.f);  // never hit, never blocks
+            mat[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            mat2[i] = make_float4(0.f, 0.f, 1.f, 1.f);
+        }
+    }
+}
+
+rt_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RT_OK;
+    if (e == cudaErrorMemoryAllocation) return RT_ERR_OOM;
+    return RT_ERR_CUDA;
+}
+
+rt_status validate_params(const rt_scene* s, const rt_render_params* p) {
+    if (!s || !p) return RT_ERR_INVALID_ARG;
+    if (p->width < 1 || p->height < 1 || p->width > 32768 || p->height > 32768) return RT_ERR_INVALID_ARG;
+    if (p->max_depth < 0 || p->max_depth > RT_MAX_DEPTH) return RT_ERR_INVALID_ARG;
+    if (p->shadow_samples < 1 || p->shadow_samples > RT_MAX_SAMPLES) return RT_ERR_INVALID_ARG;
+    if (p->shading_model != RT_PHONG && p->shading_model != RT_BLINN_PHONG) return RT_ERR_INVALID_ARG;
+    if (p->out_format != RT_OUT_RGBA8 && p->out_format != RT_OUT_F32) return RT_ERR_INVALID_ARG;
+    if (!std::isfinite(p->ambient) || !std::isfinite(p->eps) || p->eps < 0.f) return RT_ERR_INVALID_ARG;
+    if (s->any_area) {
+        const int g = (int)std::lround(std::sqrt((double)p->shadow_samples));
+        if (g * g != p->shadow_samples) return RT_ERR_INVALID_ARG;
+    }
+    return RT_OK;
+}
+
+rt_status validate_camera(const rt_camera* c) {
+    if (!c) return RT_ERR_INVALID_ARG;
+    const float f[6] = {c->pos[0], c->pos[1], c->pos[2], c->yaw_deg, c->pitch_deg, c->fov_deg};
+    if (!finite_all(f, 6) || !(c->fov_deg > 0.f) || !(c->fov_deg < 180.f)) return RT_ERR_INVALID_ARG;
+    return RT_OK;
+}
+
+// Camera basis rotated by pitch (about x) then yaw (about y), computed in double.
+Frame make_frame(const rt_scene* s, const rt_camera* c, const rt_render_params* p) {
+    Frame fr;
+    std::memset(&fr, 0, sizeof(fr));
+    fr.W = p->width;
+    fr.H = p->height;
+    fr.D = p->max_depth;
+    fr.nsamp = p->shadow_samples;
+    fr.model = p->shading_model;
+    fr.fmt = p->out_format;
+    fr.ka = p->ambient;
+    fr.eps = p->eps;
+    fr.m = p->width < p->height ? p->width : p->height;
+    const double deg = M_PI / 180.0;
+    const double yw = c->yaw_deg * deg, pt = c->pitch_deg * deg, fov = c->fov_deg * deg;
+    const double cy = std::cos(yw), sy = std::sin(yw), cp = std::cos(pt), sp = std::sin(pt);
+    const double b = 1.0 / std::tan(fov / 2.0);
+    fr.cam = make_float3(c->pos[0], c->pos[1], c->pos[2]);
+    fr.right = make_float3((float)cy, 0.f, (float)-sy);
+    fr.up = make_float3((float)(-sp * sy), (float)cp, (float)(-sp * cy));
+    fr.fwd = make_float3((float)(b * cp * sy), (float)(b * sp), (float)(b * cp * cy));
+    fr.key0 = (uint32_t)(p->seed & 0xffffffffu);
+    fr.key1 = (uint32_t)(p->seed >> 32);
+    fr.vogel_n = p->shadow_samples;
+    const int g = (int)std::lround(std::sqrt((double)p->shadow_samples));
+    fr.sample_g = g > 0 ? g : 1;
+    fr.sample_g_inv = (float)(1.0 / (double)fr.sample_g);
+    (void)s;
+    return fr;
+}
+
+struct Launch {
+    int bx, by, staging;
+};
+
+rt_status resolve_launch(const rt_launch_config* cfg, Launch* L) {
+    L->bx = 16;
+    L->by = 16;
+    L->staging = 1;
+    if (cfg) {
+        if (cfg->block_x) L->bx = cfg->block_x;
+        if (cfg->block_y) L->by = cfg->block_y;
+        if (cfg->staging) L->staging = cfg->staging;
+    }
+    if (L->bx % 8 || L->by % 4 || L->bx < 8 || L->by < 4 || L->bx * L->by < 32 || L->bx * L->by > 256)
+        return RT_ERR_INVALID_ARG;
+    if (L->staging != 1 && L->staging != 2) return RT_ERR_INVALID_ARG;
+    return RT_OK;
+}
+
+int max_smem_optin() {
+    static int v = -1;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    if (v < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 48 * 1024;
+    }
+    return v;
+}
+
+template <typename K>
+rt_status ensure_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return RT_OK;
+    const int cap = max_smem_optin() - 1024;  // static shared memory of the kernels
+    if ((long long)bytes > cap) return RT_ERR_UNSUPPORTED;
+    return cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+extern "C" {
+
+const char* rt_status_string(rt_status s) {
+    switch (s) {
+        case RT_OK: return "RT_OK";
+        case RT_ERR_INVALID_ARG: return "RT_ERR_INVALID_ARG";
+        case RT_ERR_CUDA: return "RT_ERR_CUDA";
+        case RT_ERR_OOM: return "RT_ERR_OOM";
+        case RT_ERR_UNSUPPORTED: return "RT_ERR_UNSUPPORTED";
+        case RT_ERR_TIMEOUT: return "RT_ERR_TIMEOUT";
+    }
+    return "RT_ERR_UNKNOWN";
+}
+
+uint64_t rt_launch_count(void) { return g_launches.load(); }
+
+rt_status rt_scene_upload(const rt_scene_desc* desc, void* stream, rt_scene** out) {
+    if (!out) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    rt_status st = validate_desc(desc);
+    if (st != RT_OK) return st;
+    rt_scene* s = new (std::nothrow) rt_scene();
+    if (!s) return RT_ERR_OOM;
+    s->ns = desc->n_spheres;
+    s->ns_pad = pad_spheres(desc->n_spheres);
+    s->has_plane = desc->has_plane ? 1 : 0;
+    s->nl = desc->n_lights;
+    for (int l = 0; l < desc->n_lights; ++l) {
+        if (desc->lights[8 * l + 4] > 0.f) s->any_area = 1;
+        if (desc->lights[8 * l + 5] > 0.f) s->any_sphere_light = 1;
+    }
+    s->bytes = scene_bytes(s->ns_pad);
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaMalloc(&s->dev, s->bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->pinned, s->bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        rt_scene_free(s);
+        return cuda_status(e);
+    }
+    pack_host(desc, s->ns_pad, static_cast<unsigned char*>(s->pinned));
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(s->dev, s->pinned, s->bytes, cudaMemcpyHostToDevice, st_);
+    if (e == cudaSuccess) e = cudaEventRecord(s->copy_done, st_);
+    if (e != cudaSuccess) {
+        rt_scene_free(s);
+        return cuda_status(e);
+    }
+    *out = s;
+    return RT_OK;
+}
+
+rt_status rt_scene_update(rt_scene* s, const rt_scene_desc* desc, int32_t desc_on_device, void* stream) {
+    if (!s || !desc) return RT_ERR_INVALID_ARG;
+    if (desc->n_spheres != s->ns || (desc->has_plane ? 1 : 0) != s->has_plane || desc->n_lights != s->nl)
+        return RT_ERR_INVALID_ARG;
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    if (desc_on_device) {
+        if ((s->ns && !desc->spheres) || (s->nl && !desc->lights) || (s->has_plane && !desc->plane))
+            return RT_ERR_INVALID_ARG;
+        const int n = s->ns + 1;
+        rt_pack_kernel<<<(n + 255) / 256, 256, 0, st_>>>(view_of(s), s->ns, desc->spheres, s->has_plane,
+                                                         desc->plane, s->nl, desc->lights);
+        g_launches++;
+        return cuda_status(cudaGetLastError());
+    }
+    rt_status st = validate_desc(desc);
+    if (st != RT_OK) return st;
+    cudaError_t e = cudaEventSynchronize(s->copy_done);  // the previous copy has left the staging buffer
+    if (e != cudaSuccess) return cuda_status(e);
+    pack_host(desc, s->ns_pad, static_cast<unsigned char*>(s->pinned));
+    e = cudaMemcpyAsync(s->dev, s->pinned, s->bytes, cudaMemcpyHostToDevice, st_);
+    if (e == cudaSuccess) e = cudaEventRecord(s->copy_done, st_);
+    return cuda_status(e);
+}
+
+rt_status rt_scene_free(rt_scene* s) {
+    if (!s) return RT_OK;
+    cudaDeviceSynchronize();
+    if (s->dev) cudaFree(s->dev);
+    if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->copy_done) cudaEventDestroy(s->copy_done);
+    delete s;
+    return RT_OK;
+}
+
+size_t rt_scene_bytes(const rt_scene* s) { return s ? s->bytes : 0; }
+
+size_t rt_hitrec_bytes(const rt_scene* s, const rt_render_params* p) {
+    if (!s || !p || p->width < 1 || p->height < 1 || p->max_depth < 0) return 0;
+    return (size_t)(p->max_depth + 1) * (size_t)(2 + s->nl) * (size_t)p->width * (size_t)p->height * 4u;
+}
+
+rt_status rt_render(const rt_scene* s, const rt_camera* cam, const rt_render_params* p, void* out_dev,
+                    size_t out_pitch_bytes, void* hitrec_dev, const rt_launch_config* cfg, void* stream) {
+    rt_status st = validate_params(s, p);
+    if (st != RT_OK) return st;
+    if ((st = validate_camera(cam)) != RT_OK) return st;
+    const size_t row = (size_t)p->width * (p->out_format == RT_OUT_F32 ? 16 : 4);
+    if (!out_dev || (reinterpret_cast<uintptr_t>(out_dev) & 15) || out_pitch_bytes < row || (out_pitch_bytes & 15))
+        return RT_ERR_INVALID_ARG;
+    if (hitrec_dev && (reinterpret_cast<uintptr_t>(hitrec_dev) & 3)) return RT_ERR_INVALID_ARG;
+    Launch L;
+    if ((st = resolve_launch(cfg, &L)) != RT_OK) return st;
+    const Frame fr = make_frame(s, cam, p);
+    const size_t smem = sizeof(SceneHdr) + (size_t)s->ns_pad * 16;
+    if (hitrec_dev) {
+        if ((st = ensure_smem(rt_fwd_kernel<true>, smem)) != RT_OK) return st;
+    } else if ((st = ensure_smem(rt_fwd_kernel<false>, smem)) != RT_OK) {
+        return st;
+    }
+    const dim3 block(32, (L.bx * L.by) / 32);
+    const dim3 grid((p->width + L.bx - 1) / L.bx, (p->height + L.by - 1) / L.by);
+    const size_t plane = (size_t)p->width * (size_t)p->height;
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    if (hitrec_dev)
+        rt_fwd_kernel<true><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes,
+                                                        static_cast<float*>(hitrec_dev), plane, L.staging, L.bx,
+                                                        L.by);
+    else
+        rt_fwd_kernel<false><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, nullptr, plane,
+                                                         L.staging, L.bx, L.by);
+    g_launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+rt_status rt_device_errors(void* stream, uint32_t* bits) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_status(e);
+    uint32_t v = 0;
+    e = cudaMemcpyFromSymbol(&v, g_err_word, sizeof(v));
+    if (e != cudaSuccess) return cuda_status(e);
+    if (bits) *bits = v;
+    if (v) {
+        const uint32_t z = 0;
+        cudaMemcpyToSymbol(g_err_word, &z, sizeof(z));
+        return RT_ERR_TIMEOUT;
+    }
+    return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// rt_device.cuh -- device-side arithmetic of the per-pixel Whitted ray tracer of
+// arXiv 2305.07450 (Section 3), FP32, for sm_103a.  Included by the one CUDA
+// translation unit of the library (rt_api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rt.h"
+
+namespace rtd {
+
+// ------------------------------------------------------------------ vectors
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 mk3(float x, float y, float z) { return f3{x, y, z}; }
+__device__ __forceinline__ f3 add(f3 a, f3 b) { return mk3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ f3 sub(f3 a, f3 b) { return mk3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ f3 scl(f3 a, float s) { return mk3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ f3 fma3(f3 a, float s, f3 b) {  // a * s + b
+    return mk3(fmaf(a.x, s, b.x), fmaf(a.y, s, b.y), fmaf(a.z, s, b.z));
+}
+__device__ __forceinline__ float dot(f3 a, f3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ f3 xyz(float4 v) { return mk3(v.x, v.y, v.z); }
+// Unit vector with a correctly rounded reciprocal square root: ray directions and
+// light directions feed distances of tens of units, so their error is kept at
+// half an ulp per component before the multiply.
+__device__ __forceinline__ f3 normalize_rn(f3 a, float* len_out = nullptr) {
+    float l2 = dot(a, a);
+    float inv = __frsqrt_rn(l2);
+    if (len_out) *len_out = __fsqrt_rn(l2);
+    return scl(a, inv);
+}
+
+// ------------------------------------------------------------------ scene
+// Device scene blob: header, then the padded sphere tables.  The header and the
+// geometry table are staged into shared memory by every CTA; materials are read
+// through the read-only cache only at hits.
+constexpr int kPad = 8;  // sphere tables are padded to a multiple of this
+
+struct __align__(16) SceneHdr {
+    int ns;          // spheres
+    int ns_pad;      // padded count (multiple of kPad); pad entries never hit
+    int has_plane;
+    int nl;          // lights
+    float4 plane_g;  // nx, ny, nz, d
+    float4 plane_m;  // albedo r, g, b, k_s
+    float4 plane_m2; // spec_exp, reflectivity, 0, 0
+    float4 light_p[RT_MAX_LIGHTS];  // x, y, z, intensity
+    float4 light_s[RT_MAX_LIGHTS];  // area_side, sphere_radius, 0, 0
+};
+static_assert(sizeof(SceneHdr) % 16 == 0, "header must keep 16-byte alignment");
+
+// geo[i]  = (cx, cy, cz, r^2)   -- pad entries (0, 0, 0, -1): disc < 0, never hit
+// mat[i]  = (albedo r, g, b, k_s)
+// mat2[i] = (spec_exp, reflectivity, r, 1/r)
+struct SceneView {
+    const SceneHdr* hdr;
+    const float4* geo;
+    const float4* mat;
+    const float4* mat2;
+};
+
+__host__ __device__ inline size_t scene_geo_offset() { return sizeof(SceneHdr); }
+__host__ __device__ inline size_t scene_bytes(int ns_pad) { return sizeof(SceneHdr) + (size_t)ns_pad * 48; }
+__host__ __device__ inline int pad_spheres(int ns) { return (ns + kPad - 1) / kPad * kPad; }
+
+// Per-frame constants computed on the host (in double, rounded once to float).
+struct Frame {
+    int W, H, D, nsamp, model, fmt;
+    float ka, eps;
+    float inv_m;             // unused slot kept for alignment of the camera block
+    int m;                   // min(W, H): the side the NDC square spans (Section 3.2)
+    float3 cam;              // ray origin
+    float3 right, up, fwd;   // rotated camera basis; fwd already scaled by b
+    uint32_t key0, key1;     // Philox key = seed
+    int vogel_n;             // = nsamp
+    float sample_g_inv;      // 1 / g for the g x g stratified grid
+    int sample_g;
+};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11): ten rounds;
+// each multiplies two counter words by the round constants, xors the high halves
+// into the other two words with the round key, and permutes; the key advances by
+// the two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+// 24 high bits as a float in [0, 1): exact.
+__device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+// ------------------------------------------------------------------ specular power
+// x^e for x in (0, 1]: exact repeated squaring for small integer exponents (the
+// usual 32), exp2(e log2 x) otherwise.
+__device__ __forceinline__ float spec_pow(float x, float e) {
+    const int ei = (int)e;
+    if ((float)ei == e && ei >= 0 && ei <= 256) {
+        float r = 1.0f, b = x;
+        int k = ei;
+#pragma unroll 1
+        while (k) {
+            if (k & 1) r *= b;
+            b *= b;
+            k >>= 1;
+        }
+        return r;
+    }
+    return exp2f(e * __log2f(x));
+}
+
+}  // namespace rtd

@@ -1,0 +1,235 @@
+"""ctypes binding of ``librt.so`` (include/rt.h): argument marshalling only.
+
+Every step of the render runs in the library's CUDA kernels; PyTorch only
+allocates device memory and provides the stream.  There is no CPU fallback: if
+the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import scenes
+from .build import LIB
+
+RT_OK = 0
+STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM",
+          4: "RT_ERR_UNSUPPORTED", 5: "RT_ERR_TIMEOUT"}
+
+
+class RtError(RuntimeError):
+    def __init__(self, where: str, status: int):
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n_spheres", C.c_int32), ("spheres", C.c_void_p), ("has_plane", C.c_int32),
+                ("plane", C.c_void_p), ("n_lights", C.c_int32), ("lights", C.c_void_p)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("yaw_deg", C.c_float), ("pitch_deg", C.c_float),
+                ("fov_deg", C.c_float)]
+
+
+class RenderParams(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("max_depth", C.c_int32),
+                ("shadow_samples", C.c_int32), ("shading_model", C.c_int32),
+                ("out_format", C.c_int32), ("ambient", C.c_float), ("eps", C.c_float),
+                ("seed", C.c_uint64)]
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("block_x", C.c_int32), ("block_y", C.c_int32), ("staging", C.c_int32),
+                ("min_blocks_per_sm", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load librt.so (built in-tree by paper_2305_07450_b300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"{LIB} is missing: build it with `python -m paper_2305_07450_b300.build` "
+                              "(or __graft_entry__.build()); there is no fallback path")
+        L = C.CDLL(LIB)
+        vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
+        L.rt_status_string.restype = C.c_char_p
+        L.rt_status_string.argtypes = [C.c_int]
+        L.rt_scene_upload.argtypes = [C.POINTER(SceneDesc), vp, C.POINTER(vp)]
+        L.rt_scene_update.argtypes = [vp, C.POINTER(SceneDesc), i32, vp]
+        L.rt_scene_free.argtypes = [vp]
+        L.rt_render.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), vp, sz, vp,
+                                C.POINTER(LaunchConfig), vp]
+        L.rt_hitrec_bytes.argtypes = [vp, C.POINTER(RenderParams)]
+        L.rt_hitrec_bytes.restype = sz
+        L.rt_device_errors.argtypes = [vp, C.POINTER(C.c_uint32)]
+        L.rt_launch_count.restype = C.c_uint64
+        L.rt_scene_bytes.argtypes = [vp]
+        L.rt_scene_bytes.restype = sz
+        for name in ("rt_scene_upload", "rt_scene_update", "rt_scene_free", "rt_render",
+                     "rt_device_errors"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def check(where: str, st: int):
+    if st != RT_OK:
+        raise RtError(where, st)
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def camera_struct(cam) -> Camera:
+    c = np.asarray(cam, np.float32).reshape(6)
+    s = Camera()
+    s.pos[0], s.pos[1], s.pos[2] = float(c[0]), float(c[1]), float(c[2])
+    s.yaw_deg, s.pitch_deg, s.fov_deg = float(c[3]), float(c[4]), float(c[5])
+    return s
+
+
+def params_struct(p: scenes.Params) -> RenderParams:
+    s = RenderParams()
+    s.width, s.height, s.max_depth = int(p.width), int(p.height), int(p.max_depth)
+    s.shadow_samples, s.shading_model, s.out_format = int(p.shadow_samples), int(p.shading_model), int(p.out_format)
+    s.ambient, s.eps = float(p.ambient), float(p.eps)
+    s.seed = int(p.seed) & 0xFFFFFFFFFFFFFFFF
+    return s
+
+
+def launch_struct(launch) -> LaunchConfig | None:
+    if launch is None:
+        return None
+    s = LaunchConfig()
+    for k, v in dict(launch).items():
+        setattr(s, k, int(v))
+    return s
+
+
+class DeviceScene:
+    """A scene resident on the device (rt_scene_upload); freed on close()/del."""
+
+    def __init__(self, scene: scenes.Scene, stream=None):
+        self._h = C.c_void_p()
+        self.n_spheres = scene.n_spheres
+        self.n_lights = scene.n_lights
+        self.has_plane = scene.plane is not None
+        self._keep = self._desc(scene)
+        check("rt_scene_upload", lib().rt_scene_upload(C.byref(self._keep[0]), _stream(stream), C.byref(self._h)))
+
+    @staticmethod
+    def _desc(scene: scenes.Scene):
+        sph = np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 10)
+        pl = None if scene.plane is None else np.ascontiguousarray(scene.plane, np.float32)
+        lig = np.ascontiguousarray(scene.lights, np.float32).reshape(-1, 8)
+        d = SceneDesc()
+        d.n_spheres = sph.shape[0]
+        d.spheres = sph.ctypes.data if sph.size else None
+        d.has_plane = 1 if pl is not None else 0
+        d.plane = pl.ctypes.data if pl is not None else None
+        d.n_lights = lig.shape[0]
+        d.lights = lig.ctypes.data if lig.size else None
+        return d, sph, pl, lig
+
+    def update(self, scene: scenes.Scene | None = None, *, spheres: torch.Tensor | None = None,
+               plane: torch.Tensor | None = None, lights: torch.Tensor | None = None, stream=None):
+        """Overwrite the scene: from host records (scene) or device tensors."""
+        if scene is not None:
+            keep = self._desc(scene)
+            check("rt_scene_update", lib().rt_scene_update(self._h, C.byref(keep[0]), 0, _stream(stream)))
+            return
+        d = SceneDesc()
+        d.n_spheres = self.n_spheres
+        d.spheres = spheres.data_ptr() if spheres is not None else None
+        d.has_plane = 1 if self.has_plane else 0
+        d.plane = plane.data_ptr() if plane is not None else None
+        d.n_lights = self.n_lights
+        d.lights = lights.data_ptr() if lights is not None else None
+        for t in (spheres, plane, lights):
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        check("rt_scene_update", lib().rt_scene_update(self._h, C.byref(d), 1, _stream(stream)))
+
+    @property
+    def nbytes(self) -> int:
+        """Bytes of the device scene table (one host-to-device upload)."""
+        return int(lib().rt_scene_bytes(self._h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().rt_scene_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def alloc_output(params: scenes.Params, device="cuda") -> tuple[torch.Tensor, int]:
+    """Framebuffer tensor and its row pitch in bytes (a multiple of 16)."""
+    W, H = int(params.width), int(params.height)
+    if params.out_format == scenes.OUT_F32:
+        return torch.empty((H, W, 4), dtype=torch.float32, device=device), W * 16
+    words = (W + 3) // 4 * 4
+    buf = torch.empty((H, words), dtype=torch.int32, device=device)
+    return buf, words * 4
+
+
+def hitrec_bytes(dscene: DeviceScene, params: scenes.Params) -> int:
+    return int(lib().rt_hitrec_bytes(dscene.handle, C.byref(params_struct(params))))
+
+
+def render(dscene: DeviceScene, camera, params: scenes.Params, *, out: torch.Tensor | None = None,
+           pitch: int | None = None, hitrec: torch.Tensor | None = None, launch=None,
+           stream=None) -> torch.Tensor:
+    """rt_render.  Returns the framebuffer: float32 [H, W, 4] (F32) or int32 [H, W]
+    holding 0xAABBGGRR (RGBA8)."""
+    if out is None:
+        out, pitch = alloc_output(params)
+    elif pitch is None:
+        pitch = out.stride(0) * out.element_size()
+    cam, prm, cfg = camera_struct(camera), params_struct(params), launch_struct(launch)
+    hr = None
+    if hitrec is not None:
+        assert hitrec.is_cuda and hitrec.numel() * hitrec.element_size() >= hitrec_bytes(dscene, params)
+        hr = hitrec.data_ptr()
+    check("rt_render", lib().rt_render(dscene.handle, C.byref(cam), C.byref(prm), out.data_ptr(), pitch, hr,
+                                       C.byref(cfg) if cfg is not None else None, _stream(stream)))
+    if params.out_format != scenes.OUT_F32:
+        return out[:, : params.width]
+    return out
+
+
+def device_errors(stream=None) -> int:
+    bits = C.c_uint32(0)
+    st = lib().rt_device_errors(_stream(stream), C.byref(bits))
+    if st not in (RT_OK, 5):
+        raise RtError("rt_device_errors", st)
+    return int(bits.value)
+
+
+def launch_count() -> int:
+    return int(lib().rt_launch_count())
+
+
+def rgba8_to_float(img: torch.Tensor) -> torch.Tensor:
+    """Unpack 0xAABBGGRR words into uint8 channels [..., 4]."""
+    v = img.contiguous().view(torch.uint8).reshape(*img.shape, 4)
+    return v

@@ -173,6 +173,15 @@ def area_4k() -> Workload:
                             out_format=OUT_RGBA8, seed=3))
 
 
+def area_scene_1080p() -> Workload:
+    """The 4K workload's scene, lights and depth at 1920x1080 (a quarter of the
+    pixels): the profiling case of the forward kernel."""
+    w = area_4k()
+    w.name = "1920x1080_256sph_3pt1area16_d8_rgba8"
+    w.params.width, w.params.height = 1920, 1080
+    return w
+
+
 BATCH_RESOLUTIONS = ((256, 256), (640, 480), (1280, 720), (1920, 1080))
 
 
@@ -229,6 +238,7 @@ WORKLOADS = {
     "720p": whitted_720p,
     "1080p": whitted_1080p,
     "4k": area_4k,
+    "4k_scene_1080p": area_scene_1080p,
     "diff512": diff_512,
 }
 

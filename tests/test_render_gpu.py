@@ -1,0 +1,185 @@
+"""Parity of the CUDA forward render (rt_render through the C ABI) with the FP64
+oracle, element by element on the same seeded inputs."""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle_pins import light, mk, plane_rec, sphere
+from paper_2305_07450_b300 import rt, scenes as S
+from parity import compare_f32, compare_rgba8, oracle_reference
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_render(w, launch=None, hitrec=False, fmt=None):
+    p = copy.copy(w.params)
+    if fmt is not None:
+        p.out_format = fmt
+    ds = rt.DeviceScene(w.scene)
+    hr = None
+    if hitrec:
+        hr = torch.empty(rt.hitrec_bytes(ds, p) // 4, dtype=torch.float32, device="cuda")
+    img = rt.render(ds, w.camera, p, launch=launch, hitrec=hr)
+    torch.cuda.synchronize()
+    assert rt.device_errors() == 0
+    out = img.cpu().numpy()
+    ds.close()
+    return (out, hr.cpu().numpy() if hr is not None else None)
+
+
+def as_workload(name, sc, cam, p):
+    return S.Workload(name, sc, cam, p)
+
+
+def check_f32_full(w, min_plain=0.99):
+    img, _ = gpu_render(w, fmt=S.OUT_F32)
+    ref, margin, sens = oracle_reference(w)
+    ok, st = compare_f32(img[..., :3].reshape(-1, 3), ref, margin, sens, w.scene.scene_scale)
+    print(w.name, st)
+    assert st["failing"] == 0, st
+    assert st["frac_within_1e-4"] >= min_plain, st
+    assert np.all(img[..., 3] == 1.0)
+    return st
+
+
+def test_whitted_256_full_frame():
+    """256x256, 16 spheres, 1 point light, depth 1: every pixel."""
+    check_f32_full(S.whitted_256(), min_plain=0.999)
+
+
+def small_cases():
+    cam = (0, 2.5, -8, 0, -15, 60)
+    sph = [sphere((-1.5, 1, 0), 1.0, albedo=(0.9, 0.2, 0.2), refl=0.3),
+           sphere((1.2, 0.8, 1.0), 0.8, albedo=(0.2, 0.9, 0.3), refl=0.5),
+           sphere((0.2, 2.2, 2.5), 0.6, albedo=(0.3, 0.3, 0.9), refl=0.1)]
+    lig = [light((3, 6, -2), 0.8), light((-4, 5, 1), 0.6)]
+    cases = {
+        "empty": mk(camera=cam, W=8, H=8),
+        "no_lights_ambient": mk(spheres=sph, plane=plane_rec(refl=0.25), camera=cam, W=24, H=16, D=2),
+        "plane_only": mk(plane=plane_rec(), lights=lig, camera=cam, W=16, H=16),
+        "depth0": mk(spheres=sph, plane=plane_rec(), lights=lig, camera=cam, W=40, H=24, D=0),
+        "ragged_37x23_d3": mk(spheres=sph, plane=plane_rec(refl=0.25), lights=lig, camera=cam, W=37, H=23, D=3),
+        "one_pixel": mk(spheres=sph, plane=plane_rec(), lights=lig, camera=cam, W=1, H=1, D=2),
+        "portrait_30x50": mk(spheres=sph, plane=plane_rec(refl=0.25), lights=lig, camera=cam, W=30, H=50, D=2),
+        "blinn": mk(spheres=sph, plane=plane_rec(refl=0.25), lights=lig, camera=cam, W=48, H=32, D=2,
+                    model=S.BLINN_PHONG),
+        "area_light": mk(spheres=sph, plane=plane_rec(refl=0.25), lights=lig + [light((0, 6, 0), 0.9, area=1.5)],
+                         camera=cam, W=48, H=32, D=2, samples=16, seed=77),
+        "sphere_light": mk(spheres=sph, plane=plane_rec(refl=0.25), lights=[light((0, 6, 0), 0.9, srad=0.7)],
+                           camera=cam, W=48, H=32, D=1, samples=20),
+        "no_plane_deep": mk(spheres=sph, lights=lig, camera=cam, W=32, H=32, D=8),
+    }
+    return cases
+
+
+@pytest.mark.parametrize("name", sorted(small_cases()))
+def test_small_case(name):
+    sc, cam, p = small_cases()[name]
+    p.eps = 5e-4
+    check_f32_full(as_workload(name, sc, cam, p), min_plain=0.98)
+
+
+def test_empty_scene_is_black():
+    sc, cam, p = small_cases()["empty"]
+    img, _ = gpu_render(as_workload("e", sc, cam, p), fmt=S.OUT_F32)
+    assert np.all(img[..., :3] == 0.0)
+
+
+def sampled(w, n_lattice_stride, n_random, fmt):
+    img, _ = gpu_render(w, fmt=fmt)
+    px = S.pixel_lattice(w.params.width, w.params.height, n_lattice_stride, seed=3, n_random=n_random)
+    ref, margin, sens = oracle_reference(w, px)
+    g = img[px[:, 1], px[:, 0]]
+    return g, ref, margin, sens
+
+
+def test_720p_rgba8_sampled():
+    """1280x720 RGBA8, 64 spheres, 2 lights, depth 4: lattice + random pixels."""
+    w = S.whitted_720p()
+    g, ref, margin, sens = sampled(w, 23, 1500, S.OUT_RGBA8)
+    ok, st = compare_rgba8(g, ref, margin, sens, w.scene.scene_scale)
+    print(st)
+    assert st["failing"] == 0 and st["frac_within_1lsb"] >= 0.999, st
+
+
+def test_720p_f32_sampled():
+    w = S.whitted_720p()
+    g, ref, margin, sens = sampled(w, 41, 800, S.OUT_F32)
+    ok, st = compare_f32(g[:, :3], ref, margin, sens, w.scene.scene_scale)
+    print(st)
+    assert st["failing"] == 0 and st["frac_within_1e-4"] >= 0.98, st
+
+
+def test_4k_area_light_sampled():
+    """3840x2160 RGBA8, 256 spheres, 3 point + 1 area light (16 Philox samples),
+    depth 8, rendered in the bench's launch configuration; sampled pixels."""
+    w = S.area_4k()
+    g, ref, margin, sens = sampled(w, 191, 600, S.OUT_RGBA8)
+    ok, st = compare_rgba8(g, ref, margin, sens, w.scene.scene_scale)
+    print(st)
+    assert st["failing"] == 0 and st["frac_within_1lsb"] >= 0.995, st
+
+
+def test_4k_f32_sampled():
+    w = S.area_4k()
+    g, ref, margin, sens = sampled(w, 257, 300, S.OUT_F32)
+    ok, st = compare_f32(g[:, :3], ref, margin, sens, w.scene.scene_scale)
+    print(st)
+    assert st["failing"] == 0 and st["frac_within_1e-4"] >= 0.95, st
+
+
+def test_launch_shapes_and_staging_bitwise_equal():
+    w = S.whitted_720p()
+    w.params.width, w.params.height = 200, 120
+    base, _ = gpu_render(w, launch={"block_x": 16, "block_y": 16, "staging": 1})
+    for cfg in ({"block_x": 16, "block_y": 16, "staging": 2}, {"block_x": 8, "block_y": 4},
+                {"block_x": 32, "block_y": 8}, {"block_x": 8, "block_y": 32}):
+        other, _ = gpu_render(w, launch=cfg)
+        assert np.array_equal(base, other), cfg
+
+
+def test_rgba8_is_quantised_f32():
+    """RGBA8 output = the FP32 output quantised by the same FP32 rule."""
+    w = S.whitted_720p()
+    w.params.width, w.params.height = 203, 117
+    f, _ = gpu_render(w, fmt=S.OUT_F32)
+    q, _ = gpu_render(w, fmt=S.OUT_RGBA8)
+    v = np.clip(f[..., :3].astype(np.float32), np.float32(0), np.float32(1))
+    codes = np.floor((v * np.float32(255.0)).astype(np.float32) + np.float32(0.5)).astype(np.uint32)
+    want = codes[..., 0] | (codes[..., 1] << 8) | (codes[..., 2] << 16) | np.uint32(0xFF000000)
+    assert np.array_equal(q.astype(np.uint32), want)
+
+
+def test_deterministic():
+    w = S.whitted_256()
+    a, _ = gpu_render(w)
+    b, _ = gpu_render(w)
+    assert np.array_equal(a, b)
+
+
+def test_hitrec_primary_hits_match_oracle():
+    w = S.whitted_256()
+    w.params.width = w.params.height = 64
+    img, hr = gpu_render(w, hitrec=True)
+    H, W, L = 64, 64, w.scene.n_lights
+    rec = hr.reshape(w.params.max_depth + 1, 2 + L, H, W)
+    ids = rec[0, 0].view(np.int32)
+    ts = rec[0, 1]
+    bad = 0
+    for y in range(H):
+        for x in range(W):
+            o, d = oracle.primary_ray(w.scene, w.camera, w.params, x, y)
+            i, t = oracle.closest(w.scene, w.camera, w.params, o, d)
+            if ids[y, x] != i:
+                bad += 1
+            elif i >= 0:
+                assert abs(ts[y, x] - t) < 1e-4 * max(1.0, t)
+    assert bad <= 3
+
+
+def test_device_error_word_clear_after_renders():
+    gpu_render(S.whitted_256())
+    assert rt.device_errors() == 0
