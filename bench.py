@@ -306,9 +306,58 @@ def run_ours(args):
         rec["e2e"] = {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": int(ds.nbytes),
                       "d2h_bytes_per_step": int(out.numel() * out.element_size())}
     ds.close()
+    if rank == 0 and not args.no_extras:
+        rec["also"] = extras(args, dev, stream)
     if world > 1:
         dist.destroy_process_group()
     return rec
+
+
+def _time_device(fn, stream, reps, warmup=2):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extras(args, dev, stream):
+    """Secondary measurements (not the headline value): the forward render at
+    1280x720 and 1920x1080 (64 spheres, 2 lights, depth 4), and the 64-scene
+    batch as one graph-captured persistent launch against 64 per-frame launches."""
+    from paper_2305_07450_b300 import rt
+    out = {}
+    for name in ("720p", "1080p"):
+        w = workload(name)
+        ds = rt.DeviceScene(w.scene)
+        o, pitch = rt.alloc_output(w.params, device=dev)
+        ms = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o, pitch=pitch, stream=stream), stream, 20)
+        out[name] = {"workload": w.name, "frames_per_s": 1e3 / ms, "ms_per_frame": ms}
+        ds.close()
+    ws = S.batch_scenes()
+    dss = [rt.DeviceScene(w.scene) for w in ws]
+    b = rt.Batch(dss, [w.camera for w in ws], [w.params for w in ws], stream=stream)
+    ms_graph = _time_device(lambda: b.launch(stream), stream, 5)
+
+    def seq():
+        for w, d, o, pt in zip(ws, dss, b.outs, b.pitches):
+            rt.render(d, w.camera, w.params, out=o, pitch=pt, stream=stream)
+    ms_seq = _time_device(seq, stream, 3)
+    px = sum(w.params.width * w.params.height for w in ws)
+    out["batch64"] = {"workload": "64 seeded scenes, 8-512 spheres, 1-4 lights, depth 1-6, 256^2..1080p, F32",
+                      "pixels": px, "ms_graph_launch": ms_graph, "ms_64_rt_render": ms_seq,
+                      "frames_per_s_batched": 64e3 / ms_graph, "frames_per_s_per_frame_launches": 64e3 / ms_seq,
+                      "speedup": ms_seq / ms_graph}
+    b.close()
+    for d in dss:
+        d.close()
+    return out
 
 
 # ----------------------------------------------------------------- reference arm
@@ -347,6 +396,7 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 720p/1080p/batch measurements")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

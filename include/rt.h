@@ -150,6 +150,49 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *cam, const rt_render
                     void *out_dev, size_t out_pitch_bytes, void *hitrec_dev,
                     const rt_launch_config *cfg, void *stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many frames (scenes of uneven sphere counts and resolutions) rendered by ONE
+ * persistent kernel launch: the (frame, tile) work items are ordered longest
+ * first (estimated tile cost) and each CTA claims the next item with an atomic
+ * add on a work counter until none is left, restaging the scene table in shared
+ * memory when its frame changes.  Each pixel is computed exactly as rt_render
+ * computes it (bit-identical output).  Not in the paper (which renders one frame
+ * per call, Section 3.9); it serves many small scenes at once.
+ *   scenes[n], cams[n], params[n], outs_dev[n], pitches[n]: one entry per frame,
+ *   with the same meaning and rules as for rt_render (hit records are not
+ *   written).  Scenes must stay alive while the batch is in flight. */
+
+/* Device workspace bytes rt_render_batch needs (256-byte aligned buffer): a work
+ * counter, the frame table and the item list.  0 on invalid arguments. */
+size_t rt_batch_workspace_bytes(int32_t n, const rt_scene *const *scenes, const rt_render_params *params,
+                                const rt_launch_config *cfg);
+
+/* Enqueue one batched render on `stream` using the caller's workspace (no device
+ * allocation): one host-to-device copy of the work tables (pageable source,
+ * staged by the runtime before the call returns), then one kernel launch.  The
+ * caller must not reuse the workspace before the launch completes. */
+rt_status rt_render_batch(int32_t n, const rt_scene *const *scenes, const rt_camera *cams,
+                          const rt_render_params *params, void *const *outs_dev, const size_t *pitches,
+                          void *workspace_dev, size_t workspace_bytes, const rt_launch_config *cfg,
+                          void *stream);
+
+typedef struct rt_batch rt_batch;   /* a planned batch captured in a CUDA graph */
+
+/* Plan a batch: validate, build the work tables, copy them to a library-owned
+ * workspace (enqueued on `stream`), and capture a CUDA graph of {reset the work
+ * counter, persistent kernel}.  Cameras and parameters are fixed at creation;
+ * scene contents may change between launches (rt_scene_update). */
+rt_status rt_batch_create(int32_t n, const rt_scene *const *scenes, const rt_camera *cams,
+                          const rt_render_params *params, void *const *outs_dev, const size_t *pitches,
+                          const rt_launch_config *cfg, void *stream, rt_batch **out);
+
+/* Replay the batch's graph on `stream` (ordered after the creation's copy).
+ * Launches of one batch must not overlap (they share the work counter). */
+rt_status rt_batch_launch(rt_batch *batch, void *stream);
+
+/* Release a batch (synchronises the device first).  NULL is accepted. */
+rt_status rt_batch_free(rt_batch *batch);
+
 /* Bytes of the hit record of one frame: for each bounce k in 0..D and each pixel,
  * the primitive id (int32, -1 = miss), the hit distance t (float) and the visible
  * fraction of every light (float), stored plane by plane:

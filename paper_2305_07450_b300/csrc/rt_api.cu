@@ -2,23 +2,24 @@
 // One translation unit: the device error word and the kernels live here.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <numeric>
+#include <vector>
 
 #include "../../include/rt.h"
+#include "rt_batch.cuh"
 #include "rt_device.cuh"
+#include "rt_errword.cuh"
 #include "rt_stage.cuh"
 #include "rt_trace.cuh"
 
 using namespace rtd;
-
-// Device error word: bits set by bounded waits that gave up (read by
-// rt_device_errors).
-static __device__ uint32_t g_err_word;
 
 static std::atomic<uint64_t> g_launches{0};
 
@@ -67,30 +68,7 @@ __global__ void __launch_bounds__(256) rt_fwd_kernel(const SceneView sv, const F
     const int x = blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
     const int y = blockIdx.y * block_y + (warp / wpr) * 4 + (lane >> 3);
     const bool valid = x < fr.W && y < fr.H;
-    float3 c = make_float3(0.f, 0.f, 0.f);
-    if (valid) c = trace_pixel<HITREC>(sc, fr, x, y, hr, hr_plane);
-
-    if (fr.fmt == RT_OUT_F32) {
-        if (valid)
-            *reinterpret_cast<float4*>(static_cast<char*>(out) + (size_t)y * pitch + (size_t)x * 16) =
-                make_float4(c.x, c.y, c.z, 1.0f);
-    } else {
-        // four horizontally adjacent pixels (lanes 4j..4j+3) -> one 16-byte store
-        const uint32_t p0 = pack_rgba8(c);
-        const uint32_t p1 = __shfl_down_sync(0xffffffffu, p0, 1);
-        const uint32_t p2 = __shfl_down_sync(0xffffffffu, p0, 2);
-        const uint32_t p3 = __shfl_down_sync(0xffffffffu, p0, 3);
-        if ((lane & 3) == 0 && y < fr.H && x < fr.W) {
-            uint32_t* row = reinterpret_cast<uint32_t*>(static_cast<char*>(out) + (size_t)y * pitch);
-            if (x + 3 < fr.W) {
-                *reinterpret_cast<uint4*>(row + x) = make_uint4(p0, p1, p2, p3);
-            } else {
-                row[x] = p0;
-                if (x + 1 < fr.W) row[x + 1] = p1;
-                if (x + 2 < fr.W) row[x + 2] = p2;
-            }
-        }
-    }
+    render_pixel<HITREC>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
 }
 
 // Device-side packing of scene records (rt_scene_update with device pointers):
@@ -272,17 +250,20 @@ Frame make_frame(const rt_scene* s, const rt_camera* c, const rt_render_params* 
 }
 
 struct Launch {
-    int bx, by, staging;
+    int bx, by, staging, min_blocks;
 };
 
 rt_status resolve_launch(const rt_launch_config* cfg, Launch* L) {
     L->bx = 16;
-    L->by = 16;
+    L->by = 8;
     L->staging = 1;
+    L->min_blocks = 0;
     if (cfg) {
         if (cfg->block_x) L->bx = cfg->block_x;
         if (cfg->block_y) L->by = cfg->block_y;
         if (cfg->staging) L->staging = cfg->staging;
+        if (cfg->min_blocks_per_sm < 0 || cfg->min_blocks_per_sm > 32) return RT_ERR_INVALID_ARG;
+        L->min_blocks = cfg->min_blocks_per_sm;
     }
     if (L->bx % 8 || L->by % 4 || L->bx < 8 || L->by < 4 || L->bx * L->by < 32 || L->bx * L->by > 256)
         return RT_ERR_INVALID_ARG;
@@ -310,7 +291,99 @@ rt_status ensure_smem(K kernel, size_t bytes) {
     return cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
 }
 
+// ------------------------------------------------------------ batch packing
+struct BatchPlanHost {
+    std::vector<unsigned char> table;  // workspace image: head, frames, items
+    int n_items = 0;
+    size_t smem = 0;
+};
+
+// Relative cost of one tile of a frame, for the longest-first item order.
+double tile_cost(const rt_scene* s, const rt_render_params* p) {
+    double rays = 1.0;
+    // every light needs at least one shadow ray; sampled lights need shadow_samples
+    rays += (double)s->nl + (double)(s->any_area + s->any_sphere_light) * (p->shadow_samples - 1);
+    return (double)(s->ns_pad + 2) * (1.0 + p->max_depth) * rays;
+}
+
+rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams, const rt_render_params* params,
+                     void* const* outs, const size_t* pitches, const Launch& L, BatchPlanHost* plan) {
+    if (n < 1 || n > (1 << (32 - kItemTileBits)) || !scenes || !cams || !params || !outs || !pitches)
+        return RT_ERR_INVALID_ARG;
+    std::vector<BatchFrame> frames((size_t)n);
+    std::vector<int> tiles((size_t)n);
+    size_t smem = 0;
+    long long n_items = 0;
+    for (int i = 0; i < n; ++i) {
+        const rt_scene* s = scenes[i];
+        const rt_render_params* p = &params[i];
+        rt_status st = validate_params(s, p);
+        if (st != RT_OK) return st;
+        if ((st = validate_camera(&cams[i])) != RT_OK) return st;
+        const size_t row = (size_t)p->width * (p->out_format == RT_OUT_F32 ? 16 : 4);
+        if (!outs[i] || (reinterpret_cast<uintptr_t>(outs[i]) & 15) || pitches[i] < row || (pitches[i] & 15))
+            return RT_ERR_INVALID_ARG;
+        BatchFrame& B = frames[(size_t)i];
+        std::memset(&B, 0, sizeof(B));
+        B.sv = view_of(s);
+        B.fr = make_frame(s, &cams[i], p);
+        B.out = outs[i];
+        B.pitch = pitches[i];
+        B.stage_bytes = (uint32_t)(sizeof(SceneHdr) + (size_t)s->ns_pad * 16);
+        B.tiles_x = (p->width + L.bx - 1) / L.bx;
+        const long long t = (long long)B.tiles_x * ((p->height + L.by - 1) / L.by);
+        if (t >= (1ll << kItemTileBits)) return RT_ERR_UNSUPPORTED;
+        tiles[(size_t)i] = (int)t;
+        n_items += t;
+        smem = std::max(smem, (size_t)B.stage_bytes);
+    }
+    if (n_items >= (1ll << 31)) return RT_ERR_UNSUPPORTED;
+    // longest-first: frames by estimated tile cost, tiles of a frame in raster order
+    std::vector<int> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return tile_cost(scenes[a], &params[a]) > tile_cost(scenes[b], &params[b]);
+    });
+    const size_t items_off = batch_items_offset(n);
+    plan->table.assign(items_off + (size_t)n_items * 4, 0);
+    std::memcpy(plan->table.data() + batch_frames_offset(), frames.data(), (size_t)n * sizeof(BatchFrame));
+    uint32_t* items = reinterpret_cast<uint32_t*>(plan->table.data() + items_off);
+    size_t k = 0;
+    for (int f : order)
+        for (int t = 0; t < tiles[(size_t)f]; ++t) items[k++] = ((uint32_t)f << kItemTileBits) | (uint32_t)t;
+    plan->n_items = (int)n_items;
+    plan->smem = smem;
+    return RT_OK;
+}
+
+rt_status batch_grid(const Launch& L, size_t smem, int* grid) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (L.min_blocks > 0) {
+        per_sm = L.min_blocks;
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel, L.bx * L.by, smem);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    *grid = sms * std::max(per_sm, 1);
+    return RT_OK;
+}
+
 }  // namespace
+
+struct rt_batch {
+    int n = 0, n_items = 0, grid = 0;
+    Launch L{};
+    size_t smem = 0, ws_bytes = 0;
+    void* ws = nullptr;
+    void* pinned = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ready = nullptr;
+};
 
 // ============================================================ C ABI
 extern "C" {
@@ -437,6 +510,115 @@ rt_status rt_render(const rt_scene* s, const rt_camera* cam, const rt_render_par
                                                          L.staging, L.bx, L.by);
     g_launches++;
     return cuda_status(cudaGetLastError());
+}
+
+size_t rt_batch_workspace_bytes(int32_t n, const rt_scene* const* scenes, const rt_render_params* params,
+                                const rt_launch_config* cfg) {
+    Launch L;
+    if (n < 1 || !scenes || !params || resolve_launch(cfg, &L) != RT_OK) return 0;
+    size_t items = 0;
+    for (int i = 0; i < n; ++i) {
+        const rt_render_params* p = &params[i];
+        if (p->width < 1 || p->height < 1) return 0;
+        items += (size_t)((p->width + L.bx - 1) / L.bx) * (size_t)((p->height + L.by - 1) / L.by);
+    }
+    return batch_items_offset(n) + items * 4;
+}
+
+rt_status rt_render_batch(int32_t n, const rt_scene* const* scenes, const rt_camera* cams,
+                          const rt_render_params* params, void* const* outs_dev, const size_t* pitches,
+                          void* workspace_dev, size_t workspace_bytes, const rt_launch_config* cfg, void* stream) {
+    Launch L;
+    rt_status st = resolve_launch(cfg, &L);
+    if (st != RT_OK) return st;
+    BatchPlanHost plan;
+    if ((st = batch_pack(n, scenes, cams, params, outs_dev, pitches, L, &plan)) != RT_OK) return st;
+    if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) || workspace_bytes < plan.table.size())
+        return RT_ERR_INVALID_ARG;
+    if ((st = ensure_smem(rt_batch_kernel, plan.smem)) != RT_OK) return st;
+    int grid = 0;
+    if ((st = batch_grid(L, plan.smem, &grid)) != RT_OK) return st;
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    // pageable source: the runtime stages it before returning, so the vector may go
+    cudaError_t e = cudaMemcpyAsync(workspace_dev, plan.table.data(), plan.table.size(), cudaMemcpyHostToDevice, st_);
+    if (e != cudaSuccess) return cuda_status(e);
+    rt_batch_kernel<<<grid, dim3(32, (L.bx * L.by) / 32), plan.smem, st_>>>(
+        static_cast<unsigned char*>(workspace_dev), n, plan.n_items, L.staging, L.bx, L.by);
+    g_launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+rt_status rt_batch_free(rt_batch* b) {
+    if (!b) return RT_OK;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->ready) cudaEventDestroy(b->ready);
+    if (b->ws) cudaFree(b->ws);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    delete b;
+    return RT_OK;
+}
+
+rt_status rt_batch_create(int32_t n, const rt_scene* const* scenes, const rt_camera* cams,
+                          const rt_render_params* params, void* const* outs_dev, const size_t* pitches,
+                          const rt_launch_config* cfg, void* stream, rt_batch** out) {
+    if (!out) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    Launch L;
+    rt_status st = resolve_launch(cfg, &L);
+    if (st != RT_OK) return st;
+    BatchPlanHost plan;
+    if ((st = batch_pack(n, scenes, cams, params, outs_dev, pitches, L, &plan)) != RT_OK) return st;
+    if ((st = ensure_smem(rt_batch_kernel, plan.smem)) != RT_OK) return st;
+    rt_batch* b = new (std::nothrow) rt_batch();
+    if (!b) return RT_ERR_OOM;
+    b->n = n;
+    b->n_items = plan.n_items;
+    b->L = L;
+    b->smem = plan.smem;
+    b->ws_bytes = plan.table.size();
+    if ((st = batch_grid(L, plan.smem, &b->grid)) != RT_OK) {
+        rt_batch_free(b);
+        return st;
+    }
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMalloc(&b->ws, b->ws_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->pinned, b->ws_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        std::memcpy(b->pinned, plan.table.data(), b->ws_bytes);
+        e = cudaMemcpyAsync(b->ws, b->pinned, b->ws_bytes, cudaMemcpyHostToDevice, st_);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ready, st_);
+    // graph: reset the work counter, then the persistent kernel
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(b->ws, 0, sizeof(unsigned), b->cap);
+        rt_batch_kernel<<<b->grid, dim3(32, (L.bx * L.by) / 32), b->smem, b->cap>>>(
+            static_cast<unsigned char*>(b->ws), n, b->n_items, L.staging, L.bx, L.by);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        rt_batch_free(b);
+        return cuda_status(e);
+    }
+    *out = b;
+    return RT_OK;
+}
+
+rt_status rt_batch_launch(rt_batch* b, void* stream) {
+    if (!b || !b->exec) return RT_ERR_INVALID_ARG;
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamWaitEvent(st_, b->ready, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st_);
+    if (e == cudaSuccess) g_launches++;
+    return cuda_status(e);
 }
 
 rt_status rt_device_errors(void* stream, uint32_t* bits) {

@@ -1,0 +1,92 @@
+// rt_batch.cuh -- batched persistent render: many scenes of uneven sphere counts
+// and resolutions in one launch.  Work items are (scene, tile) pairs in a list
+// ordered by estimated tile cost (longest first); each CTA claims the next item
+// with one atomicAdd on a work counter until the list is exhausted, restaging the
+// scene table in shared memory whenever its scene changes.  The counter only ever
+// advances, so no CTA waits on another.
+#pragma once
+
+#include "rt_errword.cuh"
+#include "rt_stage.cuh"
+#include "rt_trace.cuh"
+
+namespace rtd {
+
+// One frame of the batch (device-resident descriptor).
+struct __align__(16) BatchFrame {
+    SceneView sv;
+    Frame fr;
+    void* out;
+    size_t pitch;
+    uint32_t stage_bytes;  // header + geometry bytes staged in shared memory
+    int tiles_x;
+};
+
+// Workspace layout (device): [counter, padded to 256 B][BatchFrame x n][item x n_items]
+// item = (frame index << 20) | tile index.
+constexpr int kItemTileBits = 20;
+constexpr size_t kWsHead = 256;
+
+__host__ __device__ inline size_t batch_frames_offset() { return kWsHead; }
+__host__ __device__ inline size_t batch_items_offset(int n) {
+    return (kWsHead + (size_t)n * sizeof(BatchFrame) + 255) / 256 * 256;
+}
+
+__global__ void __launch_bounds__(256) rt_batch_kernel(unsigned char* __restrict__ ws, int n_frames, int n_items,
+                                                       int staging, int block_x, int block_y) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ int s_item;
+    __shared__ Frame s_fr;
+    __shared__ void* s_out;
+    __shared__ size_t s_pitch;
+    __shared__ int s_tiles_x;
+    __shared__ const float4* s_mat;
+    __shared__ const float4* s_mat2;
+    unsigned* counter = reinterpret_cast<unsigned*>(ws);
+    const BatchFrame* frames = reinterpret_cast<const BatchFrame*>(ws + batch_frames_offset());
+    const uint32_t* items = reinterpret_cast<const uint32_t*>(ws + batch_items_offset(n_frames));
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (staging == 1 && tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    int cur = -1;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int wpr = block_x >> 3;
+#pragma unroll 1
+    while (true) {
+        if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;  // the same value in every thread
+        const uint32_t code = __ldg(items + it);
+        const int fi = (int)(code >> kItemTileBits);
+        const int tile = (int)(code & ((1u << kItemTileBits) - 1u));
+        if (fi != cur) {
+            const BatchFrame* B = frames + fi;
+            if (tid == 0) {
+                s_fr = B->fr;
+                s_out = B->out;
+                s_pitch = B->pitch;
+                s_tiles_x = B->tiles_x;
+                s_mat = B->sv.mat;
+                s_mat2 = B->sv.mat2;
+                // shared memory was last read by the generic proxy; order those reads
+                // before the bulk copy's writes
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            if (!stage_to_smem(smem, B->sv.hdr, B->stage_bytes, staging, &bar, phase, &g_err_word)) return;
+            cur = fi;
+        }
+        const StagedScene sc{reinterpret_cast<const SceneHdr*>(smem),
+                             reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), s_mat, s_mat2};
+        const int tx = tile % s_tiles_x, ty = tile / s_tiles_x;
+        const int x = tx * block_x + (warp % wpr) * 8 + (lane & 7);
+        const int y = ty * block_y + (warp / wpr) * 4 + (lane >> 3);
+        const bool valid = x < s_fr.W && y < s_fr.H;
+        render_pixel<false>(sc, s_fr, x, y, valid, s_out, s_pitch, nullptr, 0);
+        __syncthreads();  // every thread is done with s_item and the staged scene
+    }
+}
+
+}  // namespace rtd

@@ -33,6 +33,19 @@ __device__ __forceinline__ f3 normalize_rn(f3 a, float* len_out = nullptr) {
     return scl(a, inv);
 }
 
+// Error-free sum (Knuth's TwoSum): s + err == a + b exactly.  Used only per hit, to
+// carry ray origins as unevaluated hi + lo pairs: positions of tens of units lose
+// ~1e-6 to FP32 rounding, which a small sphere turns into ~1e-6 rad of normal.
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+__device__ __forceinline__ f3 two_sum3(f3 a, f3 b, f3& err) {
+    return mk3(two_sum(a.x, b.x, err.x), two_sum(a.y, b.y, err.y), two_sum(a.z, b.z, err.z));
+}
+
 // ------------------------------------------------------------------ scene
 // Device scene blob: header, then the padded sphere tables.  The header and the
 // geometry table are staged into shared memory by every CTA; materials are read

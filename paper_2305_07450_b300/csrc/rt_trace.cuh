@@ -78,17 +78,21 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
 }
 
 // ---------------------------------------------------------------- Section 3.6
-// Any-hit of the shadow segment from o along unit dir for length dist.  For a
-// sphere the segment is blocked iff its closest point to the centre is inside the
-// ball: tc = clamp(oc.dir, 0, dist), |oc - tc dir|^2 < r^2.  With every light
-// outside every sphere (checked at upload) this is the same predicate as "a root
-// of the ray-sphere quadratic lies in (0, dist)".  The loop runs in blocks of
-// kPad spheres and leaves once every active lane of the warp is blocked (the
-// method's early break, Section 3.6 cast-shadows listing, taken warp-wide).
-__device__ __forceinline__ bool occluded(const StagedScene& sc, f3 o, f3 dir, float dist) {
+// Any-hit of R shadow segments that leave the same origin o (one shading point):
+// segment r runs along unit dir[r] for length dist[r].  For a sphere a segment is
+// blocked iff its closest point to the centre is inside the ball:
+// tc = clamp(oc.dir, 0, dist), |oc - tc dir|^2 < r^2.  With every light outside
+// every sphere (checked at upload) this is the same predicate as "a root of the
+// ray-sphere quadratic lies in (0, dist)".  oc = c - o and the shared-memory load
+// of the sphere are shared by the R segments.  occ[r] enters true for unused
+// slots.  The loop runs in blocks of kPad spheres and leaves once every segment of
+// every active lane is blocked: the method's early break (Section 3.6 cast-shadows
+// listing), taken warp-wide.
+template <int R>
+__device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, const f3 (&dir)[4],
+                                               const float (&dist)[4], bool (&occ)[4]) {
     const float4* __restrict__ geo = sc.geo;
     const int n = sc.hdr->ns_pad;
-    bool occ = false;
     const unsigned mask = __activemask();
 #pragma unroll 1
     for (int i0 = 0; i0 < n; i0 += kPad) {
@@ -96,77 +100,235 @@ __device__ __forceinline__ bool occluded(const StagedScene& sc, f3 o, f3 dir, fl
         for (int j = 0; j < kPad; ++j) {
             const float4 g = geo[i0 + j];
             const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
-            const float tca = fmaf(ocx, dir.x, fmaf(ocy, dir.y, ocz * dir.z));
-            const float tc = fminf(fmaxf(tca, 0.0f), dist);
-            const float qx = fmaf(-tc, dir.x, ocx), qy = fmaf(-tc, dir.y, ocy), qz = fmaf(-tc, dir.z, ocz);
-            const float e = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, -g.w)));
-            occ |= (e < 0.0f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float tca = fmaf(ocx, dir[r].x, fmaf(ocy, dir[r].y, ocz * dir[r].z));
+                const float tc = fminf(fmaxf(tca, 0.0f), dist[r]);
+                const float qx = fmaf(-tc, dir[r].x, ocx), qy = fmaf(-tc, dir[r].y, ocy),
+                            qz = fmaf(-tc, dir[r].z, ocz);
+                const float e = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, -g.w)));
+                occ[r] = occ[r] || (e < 0.0f);
+            }
         }
-        if (__all_sync(mask, occ)) break;
+        bool done = true;
+#pragma unroll
+        for (int r = 0; r < R; ++r) done = done && occ[r];
+        if (__all_sync(mask, done)) break;
     }
     const SceneHdr& h = *sc.hdr;
-    if (!occ && h.has_plane) {
-        const f3 n = xyz(h.plane_g);
-        const float den = dot(dir, n);
-        const float num = -(dot(o, n) + h.plane_g.w);
-        // t = num / den in (0, dist)  <=>  same signs and |num| < dist |den|
-        if (den != 0.0f && ((num > 0.0f) == (den > 0.0f)) && num != 0.0f &&
-            fabsf(num) < dist * fabsf(den))
-            occ = true;
+    if (h.has_plane) {
+        const f3 pn = xyz(h.plane_g);
+        const float num = -(dot(o, pn) + h.plane_g.w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            // t = num / den in (0, dist)  <=>  same signs and |num| < dist |den|
+            const float den = dot(dir[r], pn);
+            if (!occ[r] && den != 0.0f && num != 0.0f && ((num > 0.0f) == (den > 0.0f)) &&
+                fabsf(num) < dist[r] * fabsf(den))
+                occ[r] = true;
+        }
     }
-    return occ;
 }
 
 // ---------------------------------------------------------------- Section 3.6.1
-// Visible fraction of a sampled light seen from p (shadow rays leave from po).
+// Target point of shadow ray s of sampled light (Lp, Ls) seen from p.
 // Square area light of side a: n = g*g strata, sample s in stratum
 // (s mod g, s div g) at ((i + xi1)/g - 1/2, (j + xi2)/g - 1/2) * a in x and z,
 // xi from Philox call s div 2 with counter (pixel, bounce, light, call), words
-// 2(s mod 2), 2(s mod 2) + 1.  Spherical light of radius R: sunflower points on the
-// great circle facing p, radius R sqrt(i/n) at angle i * phi, phi = pi (3 - sqrt 5)
-// (the angle is reduced exactly as 2 pi frac(i (3 - sqrt 5) / 2) in 32-bit fixed
-// point).
-__device__ __forceinline__ float sampled_visibility(const StagedScene& sc, const Frame& fr, uint32_t pix,
-                                                    int k, int l, f3 p, f3 po, float4 Lp, float4 Ls) {
-    int unblocked = 0;
-    const int n = fr.nsamp;
+// 2(s mod 2), 2(s mod 2) + 1 (`w` holds the call's words; refreshed on even s).
+// Spherical light of radius R: sunflower point s of n on the great circle facing p,
+// radius R sqrt(s/n) at angle s * phi, phi = pi (3 - sqrt 5) (the angle is reduced
+// exactly as 2 pi frac(s (3 - sqrt 5) / 2) in 32-bit fixed point).
+__device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k, int l, int s, f3 p,
+                                           float4 Lp, float4 Ls, uint4& w) {
     if (Ls.x > 0.0f) {
+        if ((s & 1) == 0)
+            w = philox10(make_uint4(pix, (uint32_t)k, (uint32_t)l, (uint32_t)(s >> 1)), fr.key0, fr.key1);
+        const float xi1 = u24((s & 1) ? w.z : w.x);
+        const float xi2 = u24((s & 1) ? w.w : w.y);
         const int g = fr.sample_g;
-        const float ginv = fr.sample_g_inv;
-        const float a = Ls.x;
-        uint4 w = make_uint4(0, 0, 0, 0);
-#pragma unroll 1
-        for (int s = 0; s < n; ++s) {
-            if ((s & 1) == 0) w = philox10(make_uint4(pix, (uint32_t)k, (uint32_t)l, (uint32_t)(s >> 1)), fr.key0, fr.key1);
-            const float xi1 = u24((s & 1) ? w.z : w.x);
-            const float xi2 = u24((s & 1) ? w.w : w.y);
-            const int i = s % g, j = s / g;
-            const f3 X = mk3(Lp.x + (((float)i + xi1) * ginv - 0.5f) * a, Lp.y,
-                             Lp.z + (((float)j + xi2) * ginv - 0.5f) * a);
-            float dist;
-            const f3 dir = normalize_rn(sub(X, p), &dist);
-            unblocked += occluded(sc, po, dir, dist) ? 0 : 1;
-        }
-    } else {
-        const float R = Ls.y;
-        f3 w = normalize_rn(sub(p, xyz(Lp)));
-        const f3 up = fabsf(w.y) < 0.999f ? mk3(0.f, 1.f, 0.f) : mk3(1.f, 0.f, 0.f);
-        const f3 u = normalize_rn(mk3(w.y * up.z - w.z * up.y, w.z * up.x - w.x * up.z, w.x * up.y - w.y * up.x));
-        const f3 v = mk3(u.y * w.z - u.z * w.y, u.z * w.x - u.x * w.z, u.x * w.y - u.y * w.x);
-        const float inv_n = 1.0f / (float)n;
-#pragma unroll 1
-        for (int i = 0; i < n; ++i) {
-            const float r = R * sqrtf((float)i * inv_n);
-            const uint32_t frac = (uint32_t)i * 0x61C88647u;  // 2^32 (3 - sqrt 5) / 2
-            float sn, cs;
-            sincospif((float)(frac >> 8) * (1.0f / 8388608.0f), &sn, &cs);  // 2 frac
-            const f3 X = add(xyz(Lp), add(scl(u, r * cs), scl(v, r * sn)));
-            float dist;
-            const f3 dir = normalize_rn(sub(X, p), &dist);
-            unblocked += occluded(sc, po, dir, dist) ? 0 : 1;
-        }
+        const int i = s % g, j = s / g;
+        const float a = Ls.x, ginv = fr.sample_g_inv;
+        return mk3(Lp.x + (((float)i + xi1) * ginv - 0.5f) * a, Lp.y, Lp.z + (((float)j + xi2) * ginv - 0.5f) * a);
     }
-    return (float)unblocked / (float)n;
+    const f3 wv = normalize_rn(sub(p, xyz(Lp)));
+    const f3 up = fabsf(wv.y) < 0.999f ? mk3(0.f, 1.f, 0.f) : mk3(1.f, 0.f, 0.f);
+    const f3 u = normalize_rn(mk3(wv.y * up.z - wv.z * up.y, wv.z * up.x - wv.x * up.z, wv.x * up.y - wv.y * up.x));
+    const f3 v = mk3(u.y * wv.z - u.z * wv.y, u.z * wv.x - u.x * wv.z, u.x * wv.y - u.y * wv.x);
+    const float r = Ls.y * sqrtf((float)s / (float)fr.nsamp);
+    const uint32_t frac = (uint32_t)s * 0x61C88647u;  // 2^32 (3 - sqrt 5) / 2
+    float sn, cs;
+    sincospif((float)(frac >> 8) * (1.0f / 8388608.0f), &sn, &cs);  // 2 frac
+    return add(xyz(Lp), add(scl(u, r * cs), scl(v, r * sn)));
+}
+
+// ---------------------------------------------------------------- Sections 3.5-3.6
+// Shading of one hit: A = k_a + sum_l I_l vis_l max(n.l, 0), S = sum_l I_l vis_l k_s
+// spec_l; a light is skipped when n.l <= 0.  Phong spec = max(v.r, 0)^exp with r
+// the light direction mirrored about n and v = -d; Blinn spec = max(n.h, 0)^exp.
+// The shadow rays of the hit (one per lit point light, n per lit sampled light,
+// in light order) are traced in groups of up to four from the common origin po;
+// the group size is the warp's maximum of the lanes' remaining rays.
+struct HitShade {
+    float A, S;
+};
+
+__device__ __forceinline__ float light_spec(const Frame& fr, f3 n, f3 d, f3 lh, float ndl, float e) {
+    if (fr.model == RT_PHONG) {
+        const f3 r = sub(scl(n, 2.0f * ndl), lh);
+        const float vr = -dot(d, r);
+        return vr > 0.0f ? spec_pow(vr, e) : 0.0f;
+    }
+    const f3 hv = normalize_rn(sub(lh, d));
+    const float nh = dot(n, hv);
+    return nh > 0.0f ? spec_pow(nh, e) : 0.0f;
+}
+
+__device__ __forceinline__ int rays_of_light(const Frame& fr, float4 Ls) {
+    return (Ls.x > 0.0f || Ls.y > 0.0f) ? fr.nsamp : 1;
+}
+
+template <bool HITREC>
+__device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, f3 p,
+                                              f3 p_lo, f3 n, f3 po, f3 d, float ks, float e, float* __restrict__ hr,
+                                              size_t hr_k, size_t hr_plane) {
+    const SceneHdr& h = *sc.hdr;
+    HitShade out{fr.ka, 0.0f};
+    // lights on the lit side and the number of shadow rays they need
+    uint32_t lit = 0;
+    int total = 0;
+#pragma unroll 1
+    for (int li = 0; li < h.nl; ++li) {
+        const f3 lh = normalize_rn(sub(sub(xyz(h.light_p[li]), p), p_lo));
+        if (dot(n, lh) > 0.0f) {
+            lit |= 1u << li;
+            total += rays_of_light(fr, h.light_s[li]);
+        }
+        if (HITREC) hr[hr_k + (size_t)(2 + li) * hr_plane] = 0.0f;
+    }
+    // cursor (cl, cs): light and sample of this lane's next ray to attribute
+    int cl = lit ? __ffs(lit) - 1 : 0, cs = 0, cnt = 0;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    int done = 0;
+    const unsigned mask = __activemask();
+#pragma unroll 1
+    while (true) {
+        const int kr = min(4, total - done);
+        const int R = (int)__reduce_max_sync(mask, (unsigned)kr);
+        if (R == 0) break;
+        f3 dir[4];
+        float dist[4];
+        bool occ[4];
+        int l = cl, s = cs;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            dir[j] = mk3(0.f, 1.f, 0.f);
+            dist[j] = 0.0f;
+            occ[j] = true;
+            if (j < kr) {
+                const float4 Lp = h.light_p[l];
+                const float4 Ls = h.light_s[l];
+                const int nr = rays_of_light(fr, Ls);
+                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
+                                                                   : xyz(Lp);
+                dir[j] = normalize_rn(sub(sub(X, p), p_lo), &dist[j]);
+                occ[j] = false;
+                if (++s == nr) {
+                    s = 0;
+                    const uint32_t rest = lit & ~((2u << l) - 1u);
+                    l = rest ? __ffs(rest) - 1 : 0;
+                }
+            }
+        }
+        switch (R) {
+            case 1: occluded_group<1>(sc, po, dir, dist, occ); break;
+            case 2: occluded_group<2>(sc, po, dir, dist, occ); break;
+            case 3: occluded_group<3>(sc, po, dir, dist, occ); break;
+            default: occluded_group<4>(sc, po, dir, dist, occ); break;
+        }
+        // attribute the results to their lights in the same order
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < kr) {
+                cnt += occ[j] ? 0 : 1;
+                const float4 Lp = h.light_p[cl];
+                const int nr = rays_of_light(fr, h.light_s[cl]);
+                if (++cs == nr) {
+                    const float vis = (float)cnt / (float)nr;
+                    const f3 lh = normalize_rn(sub(sub(xyz(Lp), p), p_lo));
+                    const float ndl = dot(n, lh);
+                    const float sp = light_spec(fr, n, d, lh, ndl, e);
+                    const float iv = Lp.w * vis;
+                    out.A = fmaf(iv, ndl, out.A);
+                    out.S = fmaf(iv * ks, sp, out.S);
+                    if (HITREC) hr[hr_k + (size_t)(2 + cl) * hr_plane] = vis;
+                    cs = 0;
+                    cnt = 0;
+                    const uint32_t rest = lit & ~((2u << cl) - 1u);
+                    cl = rest ? __ffs(rest) - 1 : 0;
+                }
+            }
+        }
+        done += kr;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------- hit geometry
+// Hit point and face-forwarded normal (sphere (p - c)/r, plane n; flipped to face
+// the incoming ray), computed once per hit with the ray origin as a hi + lo pair.
+// Sphere: oc = c - o exactly (TwoSum), l = oc - (oc.d) d with the along-d residual
+// of the rounded oc.d projected out, s = sqrt(r^2 - |l|^2), p - c = -+s d - l (near
+// root, else far root): |p - c| = r to FP32 rounding, no cancellation of long
+// vectors.  The point is returned as p_hi + p_lo.  flip = -1 when the normal was
+// flipped (n = flip * n_raw).
+struct HitGeom {
+    f3 p, p_lo, n;
+    float flip;
+    float4 m, m2;   // albedo + k_s; exponent, reflectivity, r, 1/r
+};
+
+__device__ __forceinline__ HitGeom hit_geometry(const StagedScene& sc, int id, f3 o, f3 o_lo, f3 d, float t) {
+    const SceneHdr& h = *sc.hdr;
+    HitGeom hg;
+    if (id < h.ns) {
+        const float4 g = sc.geo[id];
+        hg.m = __ldg(sc.mat + id);
+        hg.m2 = __ldg(sc.mat2 + id);
+        f3 e;
+        const f3 och = two_sum3(xyz(g), scl(o, -1.0f), e);
+        const f3 ocl = sub(e, o_lo);  // oc = och + ocl exactly up to the lo rounding
+        const float tca = dot(och, d) + dot(ocl, d);
+        f3 l = add(fma3(d, -tca, och), ocl);
+        l = fma3(d, -dot(l, d), l);
+        const float disc = fmaf(-l.x, l.x, fmaf(-l.y, l.y, fmaf(-l.z, l.z, g.w)));
+        const float sq = __fsqrt_rn(fmaxf(disc, 0.0f));
+        const float sgn = (tca - sq > 0.0f) ? -sq : sq;  // near root, else far root
+        const f3 pc = mk3(fmaf(sgn, d.x, -l.x), fmaf(sgn, d.y, -l.y), fmaf(sgn, d.z, -l.z));
+        hg.p = two_sum3(xyz(g), pc, hg.p_lo);
+        hg.n = scl(pc, hg.m2.w);
+    } else {
+        hg.m = h.plane_m;
+        hg.m2 = h.plane_m2;
+        f3 e;
+        hg.p = two_sum3(o, scl(d, t), e);
+        hg.p_lo = add(e, o_lo);
+        hg.n = xyz(h.plane_g);
+    }
+    hg.flip = 1.0f;
+    if (dot(hg.n, d) > 0.0f) {
+        hg.n = scl(hg.n, -1.0f);
+        hg.flip = -1.0f;
+    }
+    return hg;
+}
+
+// Secondary ray origin p + eps n as a hi + lo pair.
+__device__ __forceinline__ f3 offset_origin(const HitGeom& hg, float eps, f3& lo) {
+    f3 e;
+    const f3 hi = two_sum3(hg.p, scl(hg.n, eps), e);
+    lo = add(e, hg.p_lo);
+    return hi;
 }
 
 // ---------------------------------------------------------------- Sections 3.5-3.7
@@ -179,11 +341,10 @@ __device__ __forceinline__ float sampled_visibility(const StagedScene& sc, const
 // T(A c + S); a miss ends the path.  HITREC: write (id, t, vis_l) per bounce.
 template <bool HITREC>
 __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame& fr, int x, int y,
-                                              float* __restrict__ hr, size_t hr_plane) {
+                                              float* __restrict__ hr, size_t hr_plane, size_t hr_pix) {
     const SceneHdr& h = *sc.hdr;
     const uint32_t pix = (uint32_t)y * (uint32_t)fr.W + (uint32_t)x;
-    const size_t hr_pix = (size_t)y * (size_t)fr.W + (size_t)x;
-    f3 o = mk3(fr.cam.x, fr.cam.y, fr.cam.z);
+    f3 o = mk3(fr.cam.x, fr.cam.y, fr.cam.z), o_lo = mk3(0.f, 0.f, 0.f);
     f3 d = primary_dir(fr, x, y);
     float T = 1.0f;
     float3 out = make_float3(0.f, 0.f, 0.f);
@@ -198,58 +359,13 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
             rec[hr_plane] = t;
         }
         if (id < 0) break;
-        // hit point and face-forwarded normal
-        f3 p, n;
-        float4 m, m2;
-        if (id < h.ns) {
-            const float4 g = sc.geo[id];
-            m = __ldg(sc.mat + id);
-            m2 = __ldg(sc.mat2 + id);
-            const f3 oc = sub(xyz(g), o);
-            const float tca = dot(oc, d);
-            const f3 l = fma3(d, -tca, oc);
-            const f3 pc = fma3(d, t - tca, scl(l, -1.0f));  // p - c = (t - tca) d - l
-            p = add(xyz(g), pc);
-            n = scl(pc, m2.w);
-        } else {
-            m = h.plane_m;
-            m2 = h.plane_m2;
-            p = fma3(d, t, o);
-            n = xyz(h.plane_g);
-        }
-        if (dot(n, d) > 0.0f) n = scl(n, -1.0f);
-        const f3 po = fma3(n, fr.eps, p);
-        // shading with shadows
-        float A = fr.ka, S = 0.0f;
-#pragma unroll 1
-        for (int li = 0; li < h.nl; ++li) {
-            const float4 Lp = h.light_p[li];
-            const float4 Ls = h.light_s[li];
-            float dist;
-            const f3 lh = normalize_rn(sub(xyz(Lp), p), &dist);
-            const float ndl = dot(n, lh);
-            float vis = 0.0f;
-            if (ndl > 0.0f) {
-                if (Ls.x > 0.0f || Ls.y > 0.0f)
-                    vis = sampled_visibility(sc, fr, pix, k, li, p, po, Lp, Ls);
-                else
-                    vis = occluded(sc, po, lh, dist) ? 0.0f : 1.0f;
-                float sp;
-                if (fr.model == RT_PHONG) {
-                    const f3 r = sub(scl(n, 2.0f * ndl), lh);
-                    const float vr = -dot(d, r);
-                    sp = vr > 0.0f ? spec_pow(vr, m2.x) : 0.0f;
-                } else {
-                    const f3 hv = normalize_rn(sub(lh, d));
-                    const float nh = dot(n, hv);
-                    sp = nh > 0.0f ? spec_pow(nh, m2.x) : 0.0f;
-                }
-                const float iv = Lp.w * vis;
-                A = fmaf(iv, ndl, A);
-                S = fmaf(iv * m.w, sp, S);
-            }
-            if (HITREC) hr[((size_t)k * (2 + h.nl) + 2 + li) * hr_plane + hr_pix] = vis;
-        }
+        const HitGeom hg = hit_geometry(sc, id, o, o_lo, d, t);
+        f3 po_lo;
+        const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);
+        const float4 m = hg.m, m2 = hg.m2;
+        const size_t hr_k = (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
+        const HitShade sh = shade_hit<HITREC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+        const float A = sh.A, S = sh.S;
         if (k < fr.D) {
             const float w = T * (1.0f - m2.y) * A;
             out.x = fmaf(w, m.x, fmaf(T, S, out.x));
@@ -258,6 +374,7 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
             T *= m2.y * A;
             d = normalize_rn(fma3(n, -2.0f * dot(d, n), d));
             o = po;
+            o_lo = po_lo;
         } else {
             const float w = T * A;
             out.x = fmaf(w, m.x, fmaf(T, S, out.x));
@@ -282,6 +399,38 @@ __device__ __forceinline__ uint32_t quant8(float v) {
 }
 __device__ __forceinline__ uint32_t pack_rgba8(float3 c) {
     return quant8(c.x) | (quant8(c.y) << 8) | (quant8(c.z) << 16) | 0xFF000000u;
+}
+
+// Trace pixel (x, y) and store it.  All 32 lanes of the warp must call (the RGBA8
+// path gathers four horizontally adjacent pixels, lanes 4j..4j+3, into one 16-byte
+// store); `valid` marks lanes whose pixel is inside the frame.
+template <bool HITREC>
+__device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
+                                             void* __restrict__ out, size_t pitch, float* __restrict__ hr,
+                                             size_t hr_plane) {
+    const int lane = threadIdx.x & 31;
+    float3 c = make_float3(0.f, 0.f, 0.f);
+    if (valid) c = trace_pixel<HITREC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
+    if (fr.fmt == RT_OUT_F32) {
+        if (valid)
+            *reinterpret_cast<float4*>(static_cast<char*>(out) + (size_t)y * pitch + (size_t)x * 16) =
+                make_float4(c.x, c.y, c.z, 1.0f);
+    } else {
+        const uint32_t p0 = pack_rgba8(c);
+        const uint32_t p1 = __shfl_down_sync(0xffffffffu, p0, 1);
+        const uint32_t p2 = __shfl_down_sync(0xffffffffu, p0, 2);
+        const uint32_t p3 = __shfl_down_sync(0xffffffffu, p0, 3);
+        if ((lane & 3) == 0 && y < fr.H && x < fr.W) {
+            uint32_t* row = reinterpret_cast<uint32_t*>(static_cast<char*>(out) + (size_t)y * pitch);
+            if (x + 3 < fr.W) {
+                *reinterpret_cast<uint4*>(row + x) = make_uint4(p0, p1, p2, p3);
+            } else {
+                row[x] = p0;
+                if (x + 1 < fr.W) row[x + 1] = p1;
+                if (x + 2 < fr.W) row[x + 2] = p2;
+            }
+        }
+    }
 }
 
 }  // namespace rtd

@@ -73,8 +73,18 @@ def lib():
         L.rt_launch_count.restype = C.c_uint64
         L.rt_scene_bytes.argtypes = [vp]
         L.rt_scene_bytes.restype = sz
+        PP = C.POINTER(vp)
+        L.rt_batch_workspace_bytes.argtypes = [i32, PP, C.POINTER(RenderParams), C.POINTER(LaunchConfig)]
+        L.rt_batch_workspace_bytes.restype = sz
+        L.rt_render_batch.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
+                                      C.POINTER(sz), vp, sz, C.POINTER(LaunchConfig), vp]
+        L.rt_batch_create.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
+                                      C.POINTER(sz), C.POINTER(LaunchConfig), vp, C.POINTER(vp)]
+        L.rt_batch_launch.argtypes = [vp, vp]
+        L.rt_batch_free.argtypes = [vp]
         for name in ("rt_scene_upload", "rt_scene_update", "rt_scene_free", "rt_render",
-                     "rt_device_errors"):
+                     "rt_device_errors", "rt_render_batch", "rt_batch_create", "rt_batch_launch",
+                     "rt_batch_free"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -233,3 +243,82 @@ def rgba8_to_float(img: torch.Tensor) -> torch.Tensor:
     """Unpack 0xAABBGGRR words into uint8 channels [..., 4]."""
     v = img.contiguous().view(torch.uint8).reshape(*img.shape, 4)
     return v
+
+
+# ------------------------------------------------------------------ batches
+def _batch_arrays(dscenes, cameras, params_list, outs, pitches):
+    n = len(dscenes)
+    sc = (C.c_void_p * n)(*[d.handle.value for d in dscenes])
+    cams = (Camera * n)(*[camera_struct(c) for c in cameras])
+    prm = (RenderParams * n)(*[params_struct(p) for p in params_list])
+    op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    pt = (C.c_size_t * n)(*[int(p) for p in pitches])
+    return n, sc, cams, prm, op, pt
+
+
+def alloc_batch_outputs(params_list, device="cuda"):
+    outs, pitches = [], []
+    for p in params_list:
+        o, pt = alloc_output(p, device)
+        outs.append(o)
+        pitches.append(pt)
+    return outs, pitches
+
+
+def batch_workspace_bytes(dscenes, params_list, launch=None) -> int:
+    n = len(dscenes)
+    sc = (C.c_void_p * n)(*[d.handle.value for d in dscenes])
+    prm = (RenderParams * n)(*[params_struct(p) for p in params_list])
+    cfg = launch_struct(launch)
+    return int(lib().rt_batch_workspace_bytes(n, sc, prm, C.byref(cfg) if cfg is not None else None))
+
+
+def render_batch(dscenes, cameras, params_list, *, outs=None, pitches=None, workspace=None, launch=None,
+                 stream=None):
+    """rt_render_batch: one persistent-kernel launch over every frame, with a
+    caller-owned device workspace (allocated here as a torch tensor if None)."""
+    if outs is None:
+        outs, pitches = alloc_batch_outputs(params_list)
+    ws_bytes = batch_workspace_bytes(dscenes, params_list, launch)
+    if workspace is None:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    n, sc, cams, prm, op, pt = _batch_arrays(dscenes, cameras, params_list, outs, pitches)
+    cfg = launch_struct(launch)
+    check("rt_render_batch", lib().rt_render_batch(n, sc, cams, prm, op, pt, workspace.data_ptr(),
+                                                   workspace.numel() * workspace.element_size(),
+                                                   C.byref(cfg) if cfg is not None else None, _stream(stream)))
+    return [o[:, : p.width] if p.out_format != scenes.OUT_F32 else o for o, p in zip(outs, params_list)], workspace
+
+
+class Batch:
+    """rt_batch_create / rt_batch_launch: the batch planned once and replayed as a
+    CUDA graph {reset work counter, persistent kernel}."""
+
+    def __init__(self, dscenes, cameras, params_list, *, outs=None, pitches=None, launch=None, stream=None):
+        if outs is None:
+            outs, pitches = alloc_batch_outputs(params_list)
+        self.outs, self.pitches, self.params = outs, pitches, params_list
+        self._scenes = list(dscenes)  # keep the scenes alive
+        n, sc, cams, prm, op, pt = _batch_arrays(dscenes, cameras, params_list, outs, pitches)
+        cfg = launch_struct(launch)
+        self._h = C.c_void_p()
+        check("rt_batch_create", lib().rt_batch_create(n, sc, cams, prm, op, pt,
+                                                       C.byref(cfg) if cfg is not None else None,
+                                                       _stream(stream), C.byref(self._h)))
+
+    def launch(self, stream=None):
+        check("rt_batch_launch", lib().rt_batch_launch(self._h, _stream(stream)))
+
+    def outputs(self):
+        return [o[:, : p.width] if p.out_format != scenes.OUT_F32 else o for o, p in zip(self.outs, self.params)]
+
+    def close(self):
+        if self._h:
+            lib().rt_batch_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
