@@ -42,7 +42,9 @@ typedef enum {
     RT_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed                 */
     RT_ERR_OOM = 3,           /* device or pinned host allocation failed              */
     RT_ERR_UNSUPPORTED = 4,   /* valid input outside what this build handles          */
-    RT_ERR_TIMEOUT = 5        /* a bounded device wait gave up (see rt_device_errors) */
+    RT_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (see rt_device_errors) */
+    RT_ERR_EXCEEDS_SCRATCH = 6 /* the work does not fit the fixed scratch of
+                                  rt_render_batch_noalloc                             */
 } rt_status;
 
 enum { RT_PHONG = 0, RT_BLINN_PHONG = 1 };          /* Section 3.5.1 / 3.5.2           */
@@ -192,6 +194,30 @@ rt_status rt_batch_launch(rt_batch *batch, void *stream);
 
 /* Release a batch (synchronises the device first).  NULL is accepted. */
 rt_status rt_batch_free(rt_batch *batch);
+
+/* Batched render that allocates nothing.  The paper has no counterpart: it is
+ * here for callers that must not allocate device memory while they render --
+ * code embedded in a host application or framework that owns every device
+ * allocation, or a latency-bound frame loop in which cudaMalloc/cudaFree would
+ * synchronise the device and could fail mid-run.  Same arguments and results as
+ * rt_render_batch minus the workspace: the work counter, frame table and item
+ * list live in one fixed scratch array of RT_NOALLOC_SCRATCH_BYTES in the
+ * library's device image (every GPU that loads the library holds it until the
+ * process exits), filled by one host-to-device copy from a static host buffer.
+ *   - At most RT_NOALLOC_MAX_FRAMES frames, and the work tables (see
+ *     rt_batch_workspace_bytes) at most RT_NOALLOC_SCRATCH_BYTES: otherwise
+ *     RT_ERR_EXCEEDS_SCRATCH and nothing is enqueued.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call reuses the same array (the copy rewrites it, including the work
+ *     counter, which it resets to zero): calls whose work overlaps on the GPU,
+ *     on any stream, race.  Order them (same stream or events). */
+#define RT_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define RT_NOALLOC_MAX_FRAMES 256
+rt_status rt_render_batch_noalloc(int32_t n, const rt_scene *const *scenes, const rt_camera *cams,
+                                  const rt_render_params *params, void *const *outs_dev, const size_t *pitches,
+                                  const rt_launch_config *cfg, void *stream);
 
 /* Bytes of the hit record of one frame: for each bounce k in 0..D and each pixel,
  * the primitive id (int32, -1 = miss), the hit distance t (float) and the visible

@@ -396,6 +396,7 @@ const char* rt_status_string(rt_status s) {
         case RT_ERR_OOM: return "RT_ERR_OOM";
         case RT_ERR_UNSUPPORTED: return "RT_ERR_UNSUPPORTED";
         case RT_ERR_TIMEOUT: return "RT_ERR_TIMEOUT";
+        case RT_ERR_EXCEEDS_SCRATCH: return "RT_ERR_EXCEEDS_SCRATCH";
     }
     return "RT_ERR_UNKNOWN";
 }
@@ -637,3 +638,117 @@ rt_status rt_device_errors(void* stream, uint32_t* bits) {
 }
 
 }  // extern "C"
+
+// ============================================================ batch without allocation
+// Scratch of rt_render_batch_noalloc: work counter, frame table and item list (the
+// workspace layout of rt_render_batch) in a fixed array of the device image.  In
+// host code `g_noalloc_scratch` only stands for the symbol; its device address
+// comes from cudaGetSymbolAddress, looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_dev_ptr[kMaxDevices] = {};
+// host image of the tables, static so that no call touches the heap
+alignas(256) unsigned char g_noalloc_host[RT_NOALLOC_SCRATCH_BYTES];
+
+// The workspace image of rt_render_batch, written into a fixed buffer without any
+// heap use (frames in longest-first order by tile cost, tiles in raster order).
+rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera* cams,
+                           const rt_render_params* params, void* const* outs, const size_t* pitches,
+                           const Launch& L, unsigned char* buf, size_t cap, size_t* bytes, int* n_items_out,
+                           size_t* smem_out) {
+    if (n < 1 || !scenes || !cams || !params || !outs || !pitches) return RT_ERR_INVALID_ARG;
+    if (n > RT_NOALLOC_MAX_FRAMES) return RT_ERR_EXCEEDS_SCRATCH;
+    int order[RT_NOALLOC_MAX_FRAMES];
+    int tiles[RT_NOALLOC_MAX_FRAMES];
+    long long n_items = 0;
+    size_t smem = 0;
+    const size_t items_off = batch_items_offset(n);
+    if (items_off > cap) return RT_ERR_EXCEEDS_SCRATCH;
+    std::memset(buf, 0, items_off);  // the work counter starts at zero
+    BatchFrame* frames = reinterpret_cast<BatchFrame*>(buf + batch_frames_offset());
+    for (int i = 0; i < n; ++i) {
+        const rt_scene* s = scenes[i];
+        const rt_render_params* p = &params[i];
+        rt_status st = validate_params(s, p);
+        if (st != RT_OK) return st;
+        if ((st = validate_camera(&cams[i])) != RT_OK) return st;
+        const size_t row = (size_t)p->width * (p->out_format == RT_OUT_F32 ? 16 : 4);
+        if (!outs[i] || (reinterpret_cast<uintptr_t>(outs[i]) & 15) || pitches[i] < row || (pitches[i] & 15))
+            return RT_ERR_INVALID_ARG;
+        BatchFrame& B = frames[i];
+        B.sv = view_of(s);
+        B.fr = make_frame(s, &cams[i], p);
+        B.out = outs[i];
+        B.pitch = pitches[i];
+        B.stage_bytes = (uint32_t)(sizeof(SceneHdr) + (size_t)s->ns_pad * 16);
+        B.tiles_x = (p->width + L.bx - 1) / L.bx;
+        const long long t = (long long)B.tiles_x * ((p->height + L.by - 1) / L.by);
+        if (t >= (1ll << kItemTileBits)) return RT_ERR_UNSUPPORTED;
+        tiles[i] = (int)t;
+        n_items += t;
+        smem = std::max(smem, (size_t)B.stage_bytes);
+        // insertion into the longest-first order (stable: ties keep input order)
+        const double c = tile_cost(s, p);
+        int j = i;
+        while (j > 0 && tile_cost(scenes[order[j - 1]], &params[order[j - 1]]) < c) {
+            order[j] = order[j - 1];
+            --j;
+        }
+        order[j] = i;
+    }
+    const size_t total = items_off + (size_t)n_items * 4;
+    if (total > cap) return RT_ERR_EXCEEDS_SCRATCH;
+    uint32_t* items = reinterpret_cast<uint32_t*>(buf + items_off);
+    size_t k = 0;
+    for (int oi = 0; oi < n; ++oi) {
+        const int f = order[oi];
+        for (int t = 0; t < tiles[f]; ++t) items[k++] = ((uint32_t)f << kItemTileBits) | (uint32_t)t;
+    }
+    *bytes = total;
+    *n_items_out = (int)n_items;
+    *smem_out = smem;
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_render_batch_noalloc(int32_t n, const rt_scene* const* scenes, const rt_camera* cams,
+                                             const rt_render_params* params, void* const* outs_dev,
+                                             const size_t* pitches, const rt_launch_config* cfg, void* stream) {
+    Launch L;
+    rt_status st = resolve_launch(cfg, &L);
+    if (st != RT_OK) return st;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kMaxDevices) return RT_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> guard(g_noalloc_mu);
+    // set-up, once per device, with that device current
+    if (!g_noalloc_dev_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        g_noalloc_dev_ptr[dev] = ptr;
+    }
+    size_t bytes = 0, smem = 0;
+    int n_items = 0;
+    st = batch_pack_fixed(n, scenes, cams, params, outs_dev, pitches, L, g_noalloc_host, sizeof(g_noalloc_host),
+                          &bytes, &n_items, &smem);
+    if (st != RT_OK) return st;
+    if ((st = ensure_smem(rt_batch_kernel, smem)) != RT_OK) return st;
+    int grid = 0;
+    if ((st = batch_grid(L, smem, &grid)) != RT_OK) return st;
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    // pageable source: staged by the runtime before the call returns, so the static
+    // host image is free for the next call
+    e = cudaMemcpyAsync(g_noalloc_dev_ptr[dev], g_noalloc_host, bytes, cudaMemcpyHostToDevice, st_);
+    if (e != cudaSuccess) return cuda_status(e);
+    rt_batch_kernel<<<grid, dim3(32, (L.bx * L.by) / 32), smem, st_>>>(
+        static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]), n, n_items, L.staging, L.bx, L.by);
+    g_launches++;
+    return cuda_status(cudaGetLastError());
+}

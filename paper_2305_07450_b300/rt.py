@@ -17,7 +17,7 @@ from .build import LIB
 
 RT_OK = 0
 STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM",
-          4: "RT_ERR_UNSUPPORTED", 5: "RT_ERR_TIMEOUT"}
+          4: "RT_ERR_UNSUPPORTED", 5: "RT_ERR_TIMEOUT", 6: "RT_ERR_EXCEEDS_SCRATCH"}
 
 
 class RtError(RuntimeError):
@@ -81,6 +81,9 @@ def lib():
         L.rt_batch_create.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
                                       C.POINTER(sz), C.POINTER(LaunchConfig), vp, C.POINTER(vp)]
         L.rt_batch_launch.argtypes = [vp, vp]
+        L.rt_render_batch_noalloc.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
+                                              C.POINTER(sz), C.POINTER(LaunchConfig), vp]
+        L.rt_render_batch_noalloc.restype = C.c_int
         L.rt_batch_free.argtypes = [vp]
         for name in ("rt_scene_upload", "rt_scene_update", "rt_scene_free", "rt_render",
                      "rt_device_errors", "rt_render_batch", "rt_batch_create", "rt_batch_launch",
