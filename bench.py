@@ -357,7 +357,48 @@ def extras(args, dev, stream):
     b.close()
     for d in dss:
         d.close()
+    out["fwd_adjoint"] = fwd_adjoint(dev, stream)
     return out
+
+
+def fwd_adjoint(dev, stream):
+    """512x512 differentiable workload: forward with hit record + adjoint
+    (replay) per frame, against the plain forward; then the 200-step Adam
+    inverse-rendering loop from the unperturbed parameters to a perturbed target."""
+    import torch
+    from paper_2305_07450_b300 import inverse, rt
+    w = workload("diff512")
+    p = w.params
+    ds = rt.DeviceScene(w.scene)
+    out, pitch = rt.alloc_output(p, device=dev)
+    hr = torch.empty(rt.hitrec_bytes(ds, p) // 4 + 1, dtype=torch.float32, device=dev)
+    dl = torch.randn((p.height, p.width, 4), dtype=torch.float32, device=dev,
+                     generator=torch.Generator(dev).manual_seed(0))
+    grad = torch.empty(rt.grad_count(ds), dtype=torch.float32, device=dev)
+    wsb = torch.empty(1 << 20, dtype=torch.float32, device=dev)
+    ms_fwd = _time_device(lambda: rt.render(ds, w.camera, p, out=out, pitch=pitch, stream=stream), stream, 20)
+
+    def fwd_bwd():
+        rt.render(ds, w.camera, p, out=out, pitch=pitch, hitrec=hr, stream=stream)
+        rt.render_backward(ds, w.camera, p, dl, hitrec=hr, grad=grad, workspace=wsb, stream=stream)
+    ms_fb = _time_device(fwd_bwd, stream, 20)
+    ms_bwd_recompute = _time_device(
+        lambda: rt.render_backward(ds, w.camera, p, dl, hitrec=None, grad=grad, workspace=wsb, stream=stream),
+        stream, 10)
+    ds.close()
+    truth = S.perturbed_target(w)
+    tgt = inverse.target_image(truth, w)
+    t0 = time.perf_counter()
+    res = inverse.inverse_render(w, tgt, steps=200, lr=0.05, truth=truth)
+    torch.cuda.synchronize()
+    h = res["history"]
+    return {"workload": w.name, "ms_forward": ms_fwd, "ms_forward_hitrec_plus_adjoint": ms_fb,
+            "ms_adjoint_recompute": ms_bwd_recompute, "frames_per_s_forward": 1e3 / ms_fwd,
+            "frames_per_s_fwd_adjoint": 1e3 / ms_fb, "adjoint_over_forward": ms_fb / ms_fwd,
+            "inverse_200_adam": {"lr": 0.05, "seconds": time.perf_counter() - t0, "loss_first": h[0],
+                                 "loss_last": h[-1], "loss_drop": h[0] / h[-1],
+                                 "material_rmse_before_after": res["material_rmse"],
+                                 "light_rmse_before_after": res["light_rmse"]}}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -386,6 +427,19 @@ def run_reference(args):
     }
 
 
+def profile_batch(args):
+    import torch
+    from paper_2305_07450_b300 import rt
+    ws = S.batch_scenes()
+    dss = [rt.DeviceScene(w.scene) for w in ws]
+    b = rt.Batch(dss, [w.camera for w in ws], [w.params for w in ws])
+    for _ in range(args.warmup + args.steps):
+        b.launch()
+    torch.cuda.synchronize()
+    assert rt.device_errors() == 0
+    print(json.dumps({"profile_batch": True, "launches": args.warmup + args.steps}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,9 +451,13 @@ def main(argv=None):
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the 720p/1080p/batch measurements")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="only launch the 64-scene batch graph --warmup + --steps times (a profiling target)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.profile_batch:
+        return profile_batch(args)
     rec = run_reference(args) if args.impl == "reference" else run_ours(args)
     if rec is not None:
         print(json.dumps(rec), flush=True)

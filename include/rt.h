@@ -230,6 +230,35 @@ size_t rt_hitrec_bytes(const rt_scene *scene, const rt_render_params *params);
  * rt_scene_update copy to the device.  0 for NULL. */
 size_t rt_scene_bytes(const rt_scene *scene);
 
+/* ---------------------------------------------------------------- adjoint
+ * Reverse-mode derivative of the forward render with visibility held fixed (no
+ * silhouette or shadow-edge terms), for inverse rendering.  Not in the paper.
+ * Gradient layout (floats): sphere i at 8i + {albedo r, g, b, k_s, reflectivity,
+ * centre x, y, z}; the plane at 8N + {albedo r, g, b, k_s, reflectivity, 0, 0,
+ * 0}; light l at 8(N + 1) + 4l + {position x, y, z, intensity}. */
+
+/* Number of floats of the packed gradient: 8 (N + 1) + 4 L. */
+size_t rt_grad_count(const rt_scene *scene);
+
+/* Device workspace bytes rt_render_backward needs (one partial gradient per CTA). */
+size_t rt_backward_workspace_bytes(const rt_scene *scene, const rt_render_params *params,
+                                   const rt_launch_config *cfg);
+
+/* grad_dev (rt_grad_count floats, overwritten) = sum over pixels and RGB channels
+ * of dL/dpixel * dpixel/dtheta for L = sum dL_dimg * image.
+ *   dl_dimg_dev: device buffer laid out like the F32 framebuffer (rows of width
+ *                float RGBA, dl_pitch_bytes apart, multiple of 16; A ignored).
+ *   hitrec_dev:  the hit record of rt_render for the same scene contents, camera
+ *                and params (replay), or NULL to recompute the paths (trace again,
+ *                no hit-record memory).
+ *   workspace_dev: rt_backward_workspace_bytes bytes, 16-byte aligned.
+ * Two launches (adjoint, then a fixed-order sum of the per-CTA partials): the
+ * result is reproducible bit for bit. */
+rt_status rt_render_backward(const rt_scene *scene, const rt_camera *cam, const rt_render_params *params,
+                             const float *dl_dimg_dev, size_t dl_pitch_bytes, const void *hitrec_dev,
+                             float *grad_dev, void *workspace_dev, size_t workspace_bytes,
+                             const rt_launch_config *cfg, void *stream);
+
 /* Read and clear the device error word (bit 0: a shared-memory staging wait gave
  * up; bit 1: a batch work-queue wait gave up).  Synchronises `stream`.  Returns
  * RT_ERR_TIMEOUT when a bit was set, RT_OK otherwise; *bits (nullable) receives

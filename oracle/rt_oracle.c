@@ -84,6 +84,7 @@ typedef struct {
     double margin;
     double cnt[C_NCOUNT];
     uint32_t pix;           /* y * W + x, the Philox counter word 0 */
+    int origin;             /* primitive the current ray leaves (-1: the camera) */
 } Path;
 
 /* ------------------------------------------------------------ Philox4x32-10 */
@@ -187,7 +188,10 @@ static int plane_root(v3 o, v3 dir, v3 n, double pd, double *t)
 
 /* Margin of one closest-hit ray (length units): sphere silhouettes that could
  * compete with the hit, roots near the origin, the gap to the second-nearest
- * primitive, and the plane's horizon when the plane wins or nothing is hit. */
+ * primitive, and the plane's horizon when the plane wins or nothing is hit.  The
+ * primitive the ray leaves (P->origin) has no root near the origin by
+ * construction (the origin is offset along its normal, so its roots lie at or
+ * behind -eps), and is skipped in that term. */
 static void closest_margin(Path *P, v3 o, v3 d, int best, double tb)
 {
     const Ctx *cx = P->cx;
@@ -199,7 +203,7 @@ static void closest_margin(Path *P, v3 o, v3 d, int best, double tb)
         double ld = len(sub(oc, scl(d, tca)));
         if (tca + s->r > 0.0 && (best < 0 || tca - s->r < tb)) m = fmin(m, fabs(ld - s->r));
         double disc = s->r * s->r - ld * ld;
-        if (disc >= 0.0) {
+        if (disc >= 0.0 && i != P->origin) {
             double sq = sqrt(disc);
             m = fmin(m, fabs(tca - sq));
             m = fmin(m, fabs(tca + sq));
@@ -213,7 +217,7 @@ static void closest_margin(Path *P, v3 o, v3 d, int best, double tb)
         if (best == cx->ns || best < 0) m = fmin(m, fabs(den) * cx->S);
         if (den != 0.0) {
             double tp = -(dot(o, pl->g) + pl->r) / den;
-            m = fmin(m, fabs(tp));
+            if (P->origin != cx->ns) m = fmin(m, fabs(tp));
             if (best != cx->ns && tp > 0.0) t2 = fmin(t2, tp);
         }
     }
@@ -268,8 +272,9 @@ static int occluded(Path *P, v3 o, v3 dir, double dist)
             if (disc >= 0.0) {
                 double sq = sqrt(disc);
                 double r1 = tca - sq, r2 = tca + sq;
-                m = fmin(m, fmin(fabs(r1), fabs(r1 - dist)));
-                m = fmin(m, fmin(fabs(r2), fabs(r2 - dist)));
+                m = fmin(m, fabs(r1 - dist));
+                m = fmin(m, fabs(r2 - dist));
+                if (i != P->origin) m = fmin(m, fmin(fabs(r1), fabs(r2)));
             }
         }
     }
@@ -282,7 +287,8 @@ static int occluded(Path *P, v3 o, v3 dir, double dist)
             double den = dot(dir, pl->g);
             if (den != 0.0) {
                 double tp = -(dot(o, pl->g) + pl->r) / den;
-                m = fmin(m, fmin(fabs(tp), fabs(tp - dist)));
+                m = fmin(m, fabs(tp - dist));
+                if (P->origin != cx->ns) m = fmin(m, fabs(tp));
             }
         }
     }
@@ -425,11 +431,12 @@ static void hit_geometry(const Ctx *cx, int id, v3 o, v3 d, double t, v3 *p, v3 
  * it as reflectivity / MAX_REFLECTIVITY with the same field as the Phong exponent;
  * here exponent and ratio are separate fields).  `depth` counts down as in the
  * paper; k = D - depth is the bounce index. */
-static void trace_recursive(Path *P, v3 o, v3 d, int depth, int k, double out[3])
+static void trace_recursive(Path *P, v3 o, v3 d, int depth, int k, int origin, double out[3])
 {
     const Ctx *cx = P->cx;
     P->cnt[k == 0 ? C_PRIMARY : C_REFLECT] += 1;
     double t;
+    P->origin = origin;
     int id = closest_hit(P, o, d, &t);
     if (id < 0) { out[0] = out[1] = out[2] = 0.0; return; }
     const Prim *m = &cx->prim[id];
@@ -442,10 +449,11 @@ static void trace_recursive(Path *P, v3 o, v3 d, int depth, int k, double out[3]
         v3 rd = sub(d, scl(n, 2.0 * dot(d, n)));
         v3 ro = add(p, scl(n, cx->eps));
         double rc[3];
-        trace_recursive(P, ro, rd, depth - 1, k + 1, rc);
+        trace_recursive(P, ro, rd, depth - 1, k + 1, id, rc);
         for (int c = 0; c < 3; ++c) col[c] = m->alb[c] * (1.0 - m->rho) + rc[c] * m->rho;
     }
     double A, S;
+    P->origin = id;
     shade_terms(P, k, p, n, d, m, &A, &S);
     for (int c = 0; c < 3; ++c) out[c] = col[c] * A + S;
 }
@@ -459,11 +467,13 @@ static void trace_forward(Path *P, v3 o, v3 d, double out[3])
     const Ctx *cx = P->cx;
     double T = 1.0;
     out[0] = out[1] = out[2] = 0.0;
+    P->origin = -1;
     for (int k = 0; k <= cx->D; ++k) {
         P->cnt[k == 0 ? C_PRIMARY : C_REFLECT] += 1;
         double t;
         int id = closest_hit(P, o, d, &t);
         if (id < 0) break;
+        P->origin = id;
         const Prim *m = &cx->prim[id];
         v3 p, n;
         hit_geometry(cx, id, o, d, t, &p, &n);
@@ -561,7 +571,7 @@ ORC_API int orc_trace(const orc_in *in, int mode, int n, const int32_t *xy, doub
         P.margin = INFINITY;
         v3 o, d;
         primary_ray(&cx, x, y, du, dv, &o, &d);
-        if (mode == 1) trace_recursive(&P, o, d, cx.D, 0, rgb + 3 * i);
+        if (mode == 1) trace_recursive(&P, o, d, cx.D, 0, -1, rgb + 3 * i);
         else trace_forward(&P, o, d, rgb + 3 * i);
         if (margin) margin[i] = P.margin;
     }
@@ -623,6 +633,7 @@ ORC_API int orc_closest(const orc_in *in, const double *o, const double *d, doub
     Path P;
     memset(&P, 0, sizeof(P));
     P.cx = &cx;
+    P.origin = -1;
     int id = closest_hit(&P, V(o[0], o[1], o[2]), V(d[0], d[1], d[2]), t);
     free(cx.prim);
     free(cx.light);
@@ -636,6 +647,7 @@ ORC_API int orc_occluded(const orc_in *in, const double *o, const double *d, dou
     Path P;
     memset(&P, 0, sizeof(P));
     P.cx = &cx;
+    P.origin = -1;
     int hit = occluded(&P, V(o[0], o[1], o[2]), V(d[0], d[1], d[2]), dist);
     free(cx.prim);
     free(cx.light);

@@ -14,6 +14,7 @@
 
 #include "../../include/rt.h"
 #include "rt_batch.cuh"
+#include "rt_bwd.cuh"
 #include "rt_device.cuh"
 #include "rt_errword.cuh"
 #include "rt_stage.cuh"
@@ -620,6 +621,59 @@ rt_status rt_batch_launch(rt_batch* b, void* stream) {
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st_);
     if (e == cudaSuccess) g_launches++;
     return cuda_status(e);
+}
+
+size_t rt_grad_count(const rt_scene* s) { return s ? (size_t)grad_count(s->ns, s->nl) : 0; }
+
+size_t rt_backward_workspace_bytes(const rt_scene* s, const rt_render_params* p, const rt_launch_config* cfg) {
+    Launch L;
+    if (!s || !p || p->width < 1 || p->height < 1 || resolve_launch(cfg, &L) != RT_OK) return 0;
+    const size_t ctas = (size_t)((p->width + L.bx - 1) / L.bx) * (size_t)((p->height + L.by - 1) / L.by);
+    return ctas * (size_t)grad_count(s->ns, s->nl) * 4;
+}
+
+rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_render_params* p,
+                             const float* dl_dimg_dev, size_t dl_pitch_bytes, const void* hitrec_dev,
+                             float* grad_dev, void* workspace_dev, size_t workspace_bytes,
+                             const rt_launch_config* cfg, void* stream) {
+    rt_status st = validate_params(s, p);
+    if (st != RT_OK) return st;
+    if ((st = validate_camera(cam)) != RT_OK) return st;
+    if (!dl_dimg_dev || (reinterpret_cast<uintptr_t>(dl_dimg_dev) & 15) || dl_pitch_bytes < (size_t)p->width * 16 ||
+        (dl_pitch_bytes & 15) || !grad_dev || (hitrec_dev && (reinterpret_cast<uintptr_t>(hitrec_dev) & 3)))
+        return RT_ERR_INVALID_ARG;
+    Launch L;
+    if ((st = resolve_launch(cfg, &L)) != RT_OK) return st;
+    const size_t need = rt_backward_workspace_bytes(s, p, cfg);
+    if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 15) || workspace_bytes < need)
+        return RT_ERR_INVALID_ARG;
+    const int G = grad_count(s->ns, s->nl);
+    const int nwarps = (L.bx * L.by) / 32;
+    const size_t stage = (sizeof(SceneHdr) + (size_t)s->ns_pad * 16 + 15) / 16 * 16;
+    const size_t smem = stage + (size_t)nwarps * G * 4;
+    if (hitrec_dev) {
+        if ((st = ensure_smem(rt_bwd_kernel<true>, smem)) != RT_OK) return st;
+    } else if ((st = ensure_smem(rt_bwd_kernel<false>, smem)) != RT_OK) {
+        return st;
+    }
+    const Frame fr = make_frame(s, cam, p);
+    const dim3 block(32, nwarps);
+    const dim3 grid((p->width + L.bx - 1) / L.bx, (p->height + L.by - 1) / L.by);
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    float* parts = static_cast<float*>(workspace_dev);
+    if (hitrec_dev)
+        rt_bwd_kernel<true><<<grid, block, smem, st_>>>(view_of(s), fr, dl_dimg_dev, dl_pitch_bytes,
+                                                        static_cast<const float*>(hitrec_dev), parts, G, L.staging,
+                                                        L.bx, L.by);
+    else
+        rt_bwd_kernel<false><<<grid, block, smem, st_>>>(view_of(s), fr, dl_dimg_dev, dl_pitch_bytes, nullptr, parts,
+                                                         G, L.staging, L.bx, L.by);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    rt_grad_reduce_kernel<<<(G + 255) / 256, 256, 0, st_>>>(parts, (int)(grid.x * grid.y), G, grad_dev);
+    g_launches++;
+    return cuda_status(cudaGetLastError());
 }
 
 rt_status rt_device_errors(void* stream, uint32_t* bits) {

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) rt_batch_kernel(unsigned char* __restrict
                                                        int staging, int block_x, int block_y) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
-    __shared__ int s_item;
+    __shared__ int s_item[2];
     __shared__ Frame s_fr;
     __shared__ void* s_out;
     __shared__ size_t s_pitch;
@@ -53,12 +53,16 @@ __global__ void __launch_bounds__(256) rt_batch_kernel(unsigned char* __restrict
     int cur = -1;
     const int lane = threadIdx.x, warp = threadIdx.y;
     const int wpr = block_x >> 3;
+    // the next item is claimed while the current one renders: two slots, swapped
+    // after the barrier that ends each tile
+    if (tid == 0) s_item[0] = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    int buf = 0;
 #pragma unroll 1
     while (true) {
-        if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int it = s_item;
+        const int it = s_item[buf];
         if (it >= n_items) break;  // the same value in every thread
+        if (tid == 0) s_item[buf ^ 1] = (int)atomicAdd(counter, 1u);
         const uint32_t code = __ldg(items + it);
         const int fi = (int)(code >> kItemTileBits);
         const int tile = (int)(code & ((1u << kItemTileBits) - 1u));
@@ -85,7 +89,8 @@ __global__ void __launch_bounds__(256) rt_batch_kernel(unsigned char* __restrict
         const int y = ty * block_y + (warp / wpr) * 4 + (lane >> 3);
         const bool valid = x < s_fr.W && y < s_fr.H;
         render_pixel<false>(sc, s_fr, x, y, valid, s_out, s_pitch, nullptr, 0);
-        __syncthreads();  // every thread is done with s_item and the staged scene
+        __syncthreads();  // every thread is done with this tile, its slot and the staged scene
+        buf ^= 1;
     }
 }
 

@@ -81,6 +81,13 @@ def lib():
         L.rt_batch_create.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
                                       C.POINTER(sz), C.POINTER(LaunchConfig), vp, C.POINTER(vp)]
         L.rt_batch_launch.argtypes = [vp, vp]
+        L.rt_grad_count.argtypes = [vp]
+        L.rt_grad_count.restype = sz
+        L.rt_backward_workspace_bytes.argtypes = [vp, C.POINTER(RenderParams), C.POINTER(LaunchConfig)]
+        L.rt_backward_workspace_bytes.restype = sz
+        L.rt_render_backward.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), vp, sz, vp, vp, vp, sz,
+                                         C.POINTER(LaunchConfig), vp]
+        L.rt_render_backward.restype = C.c_int
         L.rt_render_batch_noalloc.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
                                               C.POINTER(sz), C.POINTER(LaunchConfig), vp]
         L.rt_render_batch_noalloc.restype = C.c_int
@@ -325,3 +332,83 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ adjoint
+def grad_count(dscene: DeviceScene) -> int:
+    return int(lib().rt_grad_count(dscene.handle))
+
+
+def render_backward(dscene: DeviceScene, camera, params: scenes.Params, dl_dimg: torch.Tensor, *,
+                    hitrec: torch.Tensor | None = None, grad: torch.Tensor | None = None,
+                    workspace: torch.Tensor | None = None, launch=None, stream=None) -> torch.Tensor:
+    """rt_render_backward: packed gradient (rt_grad_count floats) of
+    sum(dl_dimg * image) with respect to the scene parameters."""
+    assert dl_dimg.is_cuda and dl_dimg.dtype == torch.float32 and dl_dimg.shape[-1] == 4
+    dl = dl_dimg.contiguous()
+    cam, prm, cfg = camera_struct(camera), params_struct(params), launch_struct(launch)
+    cfgp = C.byref(cfg) if cfg is not None else None
+    if grad is None:
+        grad = torch.empty(grad_count(dscene), dtype=torch.float32, device="cuda")
+    need = int(lib().rt_backward_workspace_bytes(dscene.handle, C.byref(prm), cfgp))
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
+        workspace = torch.empty(max(need, 16) // 4 + 4, dtype=torch.float32, device="cuda")
+    check("rt_render_backward", lib().rt_render_backward(
+        dscene.handle, C.byref(cam), C.byref(prm), dl.data_ptr(), dl.stride(0) * 4,
+        hitrec.data_ptr() if hitrec is not None else None, grad.data_ptr(), workspace.data_ptr(),
+        workspace.numel() * workspace.element_size(), cfgp, _stream(stream)))
+    return grad
+
+
+def unpack_grad(grad: torch.Tensor, n_spheres: int, n_lights: int):
+    """Packed gradient -> (spheres [N, 10], plane [10], lights [L, 8]) laid out
+    like the scene records (zeros where a field is not differentiated)."""
+    N, L = n_spheres, n_lights
+    gs = grad[: 8 * N].view(N, 8)
+    gp = grad[8 * N: 8 * N + 8]
+    gl = grad[8 * (N + 1):].view(L, 4)
+    sph = torch.zeros((N, 10), dtype=grad.dtype, device=grad.device)
+    sph[:, 0:3] = gs[:, 5:8]
+    sph[:, 4:7] = gs[:, 0:3]
+    sph[:, 7] = gs[:, 3]
+    sph[:, 9] = gs[:, 4]
+    pl = torch.zeros(10, dtype=grad.dtype, device=grad.device)
+    pl[4:7] = gp[0:3]
+    pl[7] = gp[3]
+    pl[9] = gp[4]
+    lig = torch.zeros((L, 8), dtype=grad.dtype, device=grad.device)
+    lig[:, 0:4] = gl
+    return sph, pl, lig
+
+
+class RenderFn(torch.autograd.Function):
+    """Differentiable render.  forward(spheres [N,10], plane [10], lights [L,8],
+    dscene, camera, params) -> image [H, W, 4] (F32, linear); backward through
+    the hand-written adjoint, replaying the hit record of the forward render.
+    The scene records are device tensors; the device scene is overwritten with
+    them (device-to-device) before each render and again before the adjoint."""
+
+    @staticmethod
+    def forward(ctx, spheres, plane, lights, dscene, camera, params):
+        p = params if params.out_format == scenes.OUT_F32 else dataclasses_replace(params)
+        sph, pl, lig = spheres.detach().contiguous(), plane.detach().contiguous(), lights.detach().contiguous()
+        dscene.update(spheres=sph, plane=pl if dscene.has_plane else None, lights=lig)
+        hr = torch.empty(hitrec_bytes(dscene, p) // 4 + 1, dtype=torch.float32, device="cuda")
+        img = render(dscene, camera, p, hitrec=hr)
+        ctx.save_for_backward(sph, pl, lig, hr)
+        ctx.dscene, ctx.camera, ctx.params = dscene, camera, p
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        sph, pl, lig, hr = ctx.saved_tensors
+        ds = ctx.dscene
+        ds.update(spheres=sph, plane=pl if ds.has_plane else None, lights=lig)
+        g = render_backward(ds, ctx.camera, ctx.params, grad_img.float(), hitrec=hr)
+        gs, gp, gl = unpack_grad(g, ds.n_spheres, ds.n_lights)
+        return gs, gp, gl, None, None, None
+
+
+def dataclasses_replace(params: scenes.Params) -> scenes.Params:
+    import dataclasses
+    return dataclasses.replace(params, out_format=scenes.OUT_F32)
