@@ -162,7 +162,8 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *cam, const rt_render
  * per call, Section 3.9); it serves many small scenes at once.
  *   scenes[n], cams[n], params[n], outs_dev[n], pitches[n]: one entry per frame,
  *   with the same meaning and rules as for rt_render (hit records are not
- *   written).  Scenes must stay alive while the batch is in flight. */
+ *   written).  Scenes must stay alive while the batch is in flight.  The batch
+ *   kernel takes CTAs of at most 128 threads (block_x * block_y <= 128). */
 
 /* Device workspace bytes rt_render_batch needs (256-byte aligned buffer): a work
  * counter, the frame table and the item list.  0 on invalid arguments. */

@@ -1,0 +1,152 @@
+"""Autotuner of the render kernels' launch shape (CTA pixel tile, staging mode).
+
+A launch configuration is measured, not guessed: every candidate CTA shape is
+timed with CUDA events on the caller's stream (median of a few launches after a
+warm-up) and the fastest is kept.  Results are cached per key
+(GPU name, sphere-count bucket, lights, bounce limit, samples, resolution, output
+format, shading model) in a JSON file: first the table shipped with the package
+(``tuned.json``, measured on B300), then the user cache
+(``$RT_AUTOTUNE_CACHE``, default ``~/.cache/paper_2305_07450_b300/autotune.json``).
+Every candidate produces bit-identical images (the per-pixel computation does not
+depend on the tile shape), so tuning never changes results.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import statistics
+import threading
+
+import torch
+
+from . import rt, scenes
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+SHIPPED = os.path.join(PKG, "tuned.json")
+
+# CTA pixel tiles (block_x, block_y): warps are 8x4 pixel patches
+FWD_CANDIDATES = [(8, 4), (8, 8), (16, 4), (16, 8), (8, 16), (32, 4), (16, 16), (32, 8), (8, 32)]
+BATCH_CANDIDATES = [(8, 4), (8, 8), (16, 4), (16, 8), (8, 16), (32, 4)]
+
+_lock = threading.Lock()
+_mem: dict[str, dict] = {}
+
+
+def user_cache_path() -> str:
+    return os.environ.get("RT_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "paper_2305_07450_b300", "autotune.json"))
+
+
+def _bucket(n: int) -> int:
+    b = 1
+    while b < max(n, 1):
+        b <<= 1
+    return b
+
+
+def gpu_name() -> str:
+    return torch.cuda.get_device_name(torch.cuda.current_device()) if torch.cuda.is_available() else "cpu"
+
+
+def key_for(scene: scenes.Scene, params: scenes.Params, kind: str = "fwd") -> str:
+    sampled = int(any(float(l[4]) > 0 or float(l[5]) > 0 for l in scene.lights))
+    return "|".join(str(v) for v in (kind, gpu_name(), _bucket(scene.n_spheres), scene.n_lights, sampled,
+                                     params.max_depth, params.shadow_samples if sampled else 1,
+                                     params.width, params.height, params.out_format, params.shading_model))
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(key: str):
+    with _lock:
+        if key in _mem:
+            return _mem[key]
+        for path in (SHIPPED, user_cache_path()):
+            table = _load(path)
+            if key in table:
+                _mem[key] = table[key]
+                return table[key]
+    return None
+
+
+def _store(key: str, entry: dict):
+    with _lock:
+        _mem[key] = entry
+        path = user_cache_path()
+        table = _load(path)
+        table[key] = entry
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        except OSError:
+            pass  # an unwritable cache only costs re-tuning
+
+
+def _time(fn, stream, reps: int) -> float:
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def tune_render(dscene: rt.DeviceScene, scene: scenes.Scene, camera, params: scenes.Params, *, reps: int = 3,
+                candidates=FWD_CANDIDATES, stream=None, force: bool = False) -> dict:
+    """Best launch for rt_render of this frame (measured, then cached)."""
+    key = key_for(scene, params, "fwd")
+    hit = None if force else lookup(key)
+    if hit is not None:
+        return hit["launch"]
+    stream = stream or torch.cuda.current_stream()
+    out, pitch = rt.alloc_output(params)
+    results = {}
+    for bx, by in candidates:
+        for staging in (1, 2):
+            launch = {"block_x": bx, "block_y": by, "staging": staging}
+            results[(bx, by, staging)] = _time(
+                lambda: rt.render(dscene, camera, params, out=out, pitch=pitch, launch=launch, stream=stream),
+                stream, reps)
+    (bx, by, staging), ms = min(results.items(), key=lambda kv: kv[1])
+    entry = {"launch": {"block_x": bx, "block_y": by, "staging": staging}, "ms": ms,
+             "candidates": {f"{a}x{b}/s{c}": round(v, 4) for (a, b, c), v in results.items()}}
+    _store(key, entry)
+    return entry["launch"]
+
+
+def tune_batch(dscenes, scene_list, cameras, params_list, *, reps: int = 3, candidates=BATCH_CANDIDATES,
+               stream=None, force: bool = False) -> dict:
+    """Best launch for a batch (the key covers every frame of the batch)."""
+    sub = sorted(key_for(s, p, "b") for s, p in zip(scene_list, params_list))
+    key = "batch|" + gpu_name() + "|" + hashlib.sha1("\n".join(sub).encode()).hexdigest()[:16]
+    hit = None if force else lookup(key)
+    if hit is not None:
+        return hit["launch"]
+    stream = stream or torch.cuda.current_stream()
+    outs, pitches = rt.alloc_batch_outputs(params_list)
+    results = {}
+    for bx, by in candidates:
+        launch = {"block_x": bx, "block_y": by}
+        b = rt.Batch(dscenes, cameras, params_list, outs=outs, pitches=pitches, launch=launch, stream=stream)
+        results[(bx, by)] = _time(lambda: b.launch(stream), stream, reps)
+        b.close()
+    (bx, by), ms = min(results.items(), key=lambda kv: kv[1])
+    entry = {"launch": {"block_x": bx, "block_y": by}, "ms": ms,
+             "candidates": {f"{a}x{b}": round(v, 4) for (a, b), v in results.items()}}
+    _store(key, entry)
+    return entry["launch"]

@@ -311,6 +311,7 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
                      void* const* outs, const size_t* pitches, const Launch& L, BatchPlanHost* plan) {
     if (n < 1 || n > (1 << (32 - kItemTileBits)) || !scenes || !cams || !params || !outs || !pitches)
         return RT_ERR_INVALID_ARG;
+    if (L.bx * L.by > kBatchMaxThreads) return RT_ERR_INVALID_ARG;
     std::vector<BatchFrame> frames((size_t)n);
     std::vector<int> tiles((size_t)n);
     size_t smem = 0;
@@ -715,6 +716,7 @@ rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera
                            const Launch& L, unsigned char* buf, size_t cap, size_t* bytes, int* n_items_out,
                            size_t* smem_out) {
     if (n < 1 || !scenes || !cams || !params || !outs || !pitches) return RT_ERR_INVALID_ARG;
+    if (L.bx * L.by > kBatchMaxThreads) return RT_ERR_INVALID_ARG;
     if (n > RT_NOALLOC_MAX_FRAMES) return RT_ERR_EXCEEDS_SCRATCH;
     int order[RT_NOALLOC_MAX_FRAMES];
     int tiles[RT_NOALLOC_MAX_FRAMES];

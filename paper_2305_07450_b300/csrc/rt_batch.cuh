@@ -25,6 +25,7 @@ struct __align__(16) BatchFrame {
 // Workspace layout (device): [counter, padded to 256 B][BatchFrame x n][item x n_items]
 // item = (frame index << 20) | tile index.
 constexpr int kItemTileBits = 20;
+constexpr int kBatchMaxThreads = 128;  // launch bounds of the batch kernel (5 CTAs per SM)
 constexpr size_t kWsHead = 256;
 
 __host__ __device__ inline size_t batch_frames_offset() { return kWsHead; }
@@ -32,7 +33,7 @@ __host__ __device__ inline size_t batch_items_offset(int n) {
     return (kWsHead + (size_t)n * sizeof(BatchFrame) + 255) / 256 * 256;
 }
 
-__global__ void __launch_bounds__(256) rt_batch_kernel(unsigned char* __restrict__ ws, int n_frames, int n_items,
+__global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restrict__ ws, int n_frames, int n_items,
                                                        int staging, int block_x, int block_y) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;

@@ -38,26 +38,39 @@ __device__ __forceinline__ f3 primary_dir(const Frame& fr, int x, int y) {
 // well-conditioned form: with oc = c - o and tca = oc.d, the squared distance of
 // the centre from the ray's line is |oc - tca d|^2, so disc = r^2 - |oc - tca d|^2
 // avoids the cancellation of tca^2 - |oc|^2 for distant spheres.  Roots tca -+
-// sqrt(disc); the near one if it is > 0, else the far one.
+// sqrt(disc); the near one if it is > 0, else the far one.  Spheres are taken in
+// blocks of kPad: the discriminants of a block are computed branch-free, and the
+// roots only when one of them is non-negative (one branch per block).
 __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, float& t_out) {
     float tb = __int_as_float(0x7f800000);  // +inf
     int best = -1;
     const float4* __restrict__ geo = sc.geo;
     const int n = sc.hdr->ns_pad;
-#pragma unroll 4
-    for (int i = 0; i < n; ++i) {
-        const float4 g = geo[i];
-        const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
-        const float tca = fmaf(ocx, d.x, fmaf(ocy, d.y, ocz * d.z));
-        const float lx = fmaf(-tca, d.x, ocx), ly = fmaf(-tca, d.y, ocy), lz = fmaf(-tca, d.z, ocz);
-        const float disc = fmaf(-lx, lx, fmaf(-ly, ly, fmaf(-lz, lz, g.w)));
-        if (disc >= 0.0f) {
-            const float s = __fsqrt_rn(disc);
-            float t = tca - s;
-            if (t <= 0.0f) t = tca + s;
-            if (t > 0.0f && t < tb) {
-                tb = t;
-                best = i;
+#pragma unroll 1
+    for (int i0 = 0; i0 < n; i0 += kPad) {
+        float disc[kPad], tca[kPad];
+        float dmax = -1.0f;
+#pragma unroll
+        for (int j = 0; j < kPad; ++j) {
+            const float4 g = geo[i0 + j];
+            const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
+            tca[j] = fmaf(ocx, d.x, fmaf(ocy, d.y, ocz * d.z));
+            const float lx = fmaf(-tca[j], d.x, ocx), ly = fmaf(-tca[j], d.y, ocy), lz = fmaf(-tca[j], d.z, ocz);
+            disc[j] = fmaf(-lx, lx, fmaf(-ly, ly, fmaf(-lz, lz, g.w)));
+            dmax = fmaxf(dmax, disc[j]);
+        }
+        if (dmax >= 0.0f) {
+#pragma unroll
+            for (int j = 0; j < kPad; ++j) {
+                if (disc[j] >= 0.0f) {
+                    const float s = __fsqrt_rn(disc[j]);
+                    float t = tca[j] - s;
+                    if (t <= 0.0f) t = tca[j] + s;
+                    if (t > 0.0f && t < tb) {
+                        tb = t;
+                        best = i0 + j;
+                    }
+                }
             }
         }
     }

@@ -52,13 +52,15 @@ _lib = None
 
 
 def lib():
-    """Load librt.so (built in-tree by paper_2305_07450_b300.build)."""
+    """Load librt.so (built in-tree by paper_2305_07450_b300.build; the
+    environment variable RT_LIBRARY may name another build of the same ABI)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise ImportError(f"{LIB} is missing: build it with `python -m paper_2305_07450_b300.build` "
+        path = os.environ.get("RT_LIBRARY", LIB)
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with `python -m paper_2305_07450_b300.build` "
                               "(or __graft_entry__.build()); there is no fallback path")
-        L = C.CDLL(LIB)
+        L = C.CDLL(path)
         vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
         L.rt_status_string.restype = C.c_char_p
         L.rt_status_string.argtypes = [C.c_int]
