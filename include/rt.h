@@ -266,6 +266,13 @@ rt_status rt_render_backward(const rt_scene *scene, const rt_camera *cam, const 
  * the word. */
 rt_status rt_device_errors(void *stream, uint32_t *bits);
 
+/* Failure-detection self-test: launches one small kernel whose bounded wait can
+ * never be satisfied (an mbarrier expecting bytes no copy delivers, with no copy
+ * issued); after `polls` polls (1 .. 2^20) it sets bit 0 of the device error
+ * word and returns.  rt_device_errors then reports RT_ERR_TIMEOUT, and the
+ * context stays usable.  The same give-up path guards every staging wait. */
+rt_status rt_selftest_wait_timeout(uint32_t polls, void *stream);
+
 /* Number of this library's kernel launches enqueued since the process started
  * (host-side count; used to report launches in benchmarks). */
 uint64_t rt_launch_count(void);

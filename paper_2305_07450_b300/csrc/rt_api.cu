@@ -49,7 +49,7 @@ static SceneView view_of(const rt_scene* s) {
 // 8 x 4 patch (lanes 0..7 = one row), so that a warp's primary and shadow rays
 // are coherent.  The scene header and geometry table are staged in shared memory
 // once per CTA.
-template <bool HITREC>
+template <bool HITREC, bool CH>
 __global__ void __launch_bounds__(256) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                      size_t pitch, float* __restrict__ hr, size_t hr_plane,
                                                      int staging, int block_x, int block_y) {
@@ -59,17 +59,35 @@ __global__ void __launch_bounds__(256) rt_fwd_kernel(const SceneView sv, const F
     if (staging == 1 && tid == 0) mbar_init(&bar, 1);
     __syncthreads();
     uint32_t phase = 0;
-    const uint32_t stage_bytes = (uint32_t)(sizeof(SceneHdr) + 16u * (uint32_t)__ldg(&sv.hdr->ns_pad));
+    // whole table: header + geometry; tiled loop: header only (geometry per warp chunk)
+    const uint32_t stage_bytes =
+        CH ? (uint32_t)sizeof(SceneHdr) : (uint32_t)(sizeof(SceneHdr) + 16u * (uint32_t)__ldg(&sv.hdr->ns_pad));
     if (!stage_to_smem(smem, sv.hdr, stage_bytes, staging, &bar, phase, &g_err_word)) return;
-    const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
-    const StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.mat, sv.mat2};
-
     const int lane = threadIdx.x, warp = threadIdx.y;
+    const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
+    float4* tab = reinterpret_cast<float4*>(smem + sizeof(SceneHdr));
+    const StagedScene sc{hdr, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)warp * kChunk : nullptr, sv.mat,
+                         sv.mat2};
+
     const int wpr = block_x >> 3;
     const int x = blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
     const int y = blockIdx.y * block_y + (warp / wpr) * 4 + (lane >> 3);
     const bool valid = x < fr.W && y < fr.H;
-    render_pixel<HITREC>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
+    render_pixel<HITREC, CH>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
+}
+
+// Failure-detection self-test: the barrier expects bytes that no copy will ever
+// deliver (none is issued), so the bounded wait must give up after `polls` polls,
+// flag the error word and return -- the path a stalled staging copy takes.
+__global__ void rt_selftest_wait_kernel(uint32_t polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, 16);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, polls);
+    if (!ok && threadIdx.x == 0) atomicOr(&g_err_word, kErrStageTimeout);
 }
 
 // Device-side packing of scene records (rt_scene_update with device pointers):
@@ -268,7 +286,7 @@ rt_status resolve_launch(const rt_launch_config* cfg, Launch* L) {
     }
     if (L->bx % 8 || L->by % 4 || L->bx < 8 || L->by < 4 || L->bx * L->by < 32 || L->bx * L->by > 256)
         return RT_ERR_INVALID_ARG;
-    if (L->staging != 1 && L->staging != 2) return RT_ERR_INVALID_ARG;
+    if (L->staging < 1 || L->staging > 3) return RT_ERR_INVALID_ARG;
     return RT_OK;
 }
 
@@ -284,6 +302,17 @@ int max_smem_optin() {
     return v;
 }
 
+// The whole geometry table is staged unless it does not fit (or the tiled loop is
+// forced with staging = 3).
+size_t stage_smem_bytes(bool chunked, int ns_pad, int nwarps) {
+    return chunked ? sizeof(SceneHdr) + (size_t)nwarps * kChunk * 16 : sizeof(SceneHdr) + (size_t)ns_pad * 16;
+}
+
+bool use_tiled_loop(const Launch& L, int ns_pad) {
+    if (L.staging == 3) return true;
+    return stage_smem_bytes(false, ns_pad, 0) + 4096 > (size_t)(max_smem_optin() - 1024);
+}
+
 template <typename K>
 rt_status ensure_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return RT_OK;
@@ -297,6 +326,7 @@ struct BatchPlanHost {
     std::vector<unsigned char> table;  // workspace image: head, frames, items
     int n_items = 0;
     size_t smem = 0;
+    bool chunked = false;
 };
 
 // Relative cost of one tile of a frame, for the longest-first item order.
@@ -314,8 +344,12 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
     if (L.bx * L.by > kBatchMaxThreads) return RT_ERR_INVALID_ARG;
     std::vector<BatchFrame> frames((size_t)n);
     std::vector<int> tiles((size_t)n);
-    size_t smem = 0;
     long long n_items = 0;
+    int max_pad = 0;
+    for (int i = 0; i < n; ++i)
+        if (scenes[i]) max_pad = std::max(max_pad, scenes[i]->ns_pad);
+    const bool chunked = use_tiled_loop(L, max_pad);
+    const size_t smem = stage_smem_bytes(chunked, max_pad, (L.bx * L.by) / 32);
     for (int i = 0; i < n; ++i) {
         const rt_scene* s = scenes[i];
         const rt_render_params* p = &params[i];
@@ -331,13 +365,12 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
         B.fr = make_frame(s, &cams[i], p);
         B.out = outs[i];
         B.pitch = pitches[i];
-        B.stage_bytes = (uint32_t)(sizeof(SceneHdr) + (size_t)s->ns_pad * 16);
+        B.stage_bytes = (uint32_t)(chunked ? sizeof(SceneHdr) : sizeof(SceneHdr) + (size_t)s->ns_pad * 16);
         B.tiles_x = (p->width + L.bx - 1) / L.bx;
         const long long t = (long long)B.tiles_x * ((p->height + L.by - 1) / L.by);
         if (t >= (1ll << kItemTileBits)) return RT_ERR_UNSUPPORTED;
         tiles[(size_t)i] = (int)t;
         n_items += t;
-        smem = std::max(smem, (size_t)B.stage_bytes);
     }
     if (n_items >= (1ll << 31)) return RT_ERR_UNSUPPORTED;
     // longest-first: frames by estimated tile cost, tiles of a frame in raster order
@@ -355,10 +388,11 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
         for (int t = 0; t < tiles[(size_t)f]; ++t) items[k++] = ((uint32_t)f << kItemTileBits) | (uint32_t)t;
     plan->n_items = (int)n_items;
     plan->smem = smem;
+    plan->chunked = chunked;
     return RT_OK;
 }
 
-rt_status batch_grid(const Launch& L, size_t smem, int* grid) {
+rt_status batch_grid(const Launch& L, size_t smem, bool chunked, int* grid) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -366,7 +400,8 @@ rt_status batch_grid(const Launch& L, size_t smem, int* grid) {
     if (L.min_blocks > 0) {
         per_sm = L.min_blocks;
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel, L.bx * L.by, smem);
+        e = chunked ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<true>, L.bx * L.by, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<false>, L.bx * L.by, smem);
         if (e != cudaSuccess) return cuda_status(e);
     }
     *grid = sms * std::max(per_sm, 1);
@@ -375,7 +410,22 @@ rt_status batch_grid(const Launch& L, size_t smem, int* grid) {
 
 }  // namespace
 
+rt_status batch_smem(bool chunked, size_t smem) {
+    return chunked ? ensure_smem(rt_batch_kernel<true>, smem) : ensure_smem(rt_batch_kernel<false>, smem);
+}
+
+void batch_launch(bool chunked, int grid, const Launch& L, size_t smem, cudaStream_t st, unsigned char* ws, int n,
+                  int n_items) {
+    const dim3 block(32, (L.bx * L.by) / 32);
+    const int hstage = L.staging == 2 ? 2 : 1;
+    if (chunked)
+        rt_batch_kernel<true><<<grid, block, smem, st>>>(ws, n, n_items, hstage, L.bx, L.by);
+    else
+        rt_batch_kernel<false><<<grid, block, smem, st>>>(ws, n, n_items, hstage, L.bx, L.by);
+}
+
 struct rt_batch {
+    bool chunked = false;
     int n = 0, n_items = 0, grid = 0;
     Launch L{};
     size_t smem = 0, ws_bytes = 0;
@@ -494,23 +544,29 @@ rt_status rt_render(const rt_scene* s, const rt_camera* cam, const rt_render_par
     Launch L;
     if ((st = resolve_launch(cfg, &L)) != RT_OK) return st;
     const Frame fr = make_frame(s, cam, p);
-    const size_t smem = sizeof(SceneHdr) + (size_t)s->ns_pad * 16;
-    if (hitrec_dev) {
-        if ((st = ensure_smem(rt_fwd_kernel<true>, smem)) != RT_OK) return st;
-    } else if ((st = ensure_smem(rt_fwd_kernel<false>, smem)) != RT_OK) {
-        return st;
-    }
-    const dim3 block(32, (L.bx * L.by) / 32);
+    const int nwarps = (L.bx * L.by) / 32;
+    const bool chunked = use_tiled_loop(L, s->ns_pad);
+    const size_t smem = stage_smem_bytes(chunked, s->ns_pad, nwarps);
+    const int hstage = L.staging == 2 ? 2 : 1;  // how the header (and the whole table) is staged
+    const dim3 block(32, nwarps);
     const dim3 grid((p->width + L.bx - 1) / L.bx, (p->height + L.by - 1) / L.by);
     const size_t plane = (size_t)p->width * (size_t)p->height;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
-    if (hitrec_dev)
-        rt_fwd_kernel<true><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes,
-                                                        static_cast<float*>(hitrec_dev), plane, L.staging, L.bx,
-                                                        L.by);
-    else
-        rt_fwd_kernel<false><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, nullptr, plane,
-                                                         L.staging, L.bx, L.by);
+    float* hr = static_cast<float*>(hitrec_dev);
+#define RT_FWD_LAUNCH(HR, CHK)                                                                                   \
+    do {                                                                                                         \
+        if ((st = ensure_smem(rt_fwd_kernel<HR, CHK>, smem)) != RT_OK) return st;                               \
+        rt_fwd_kernel<HR, CHK><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr, plane, \
+                                                          hstage, L.bx, L.by);                                  \
+    } while (0)
+    if (hr) {
+        if (chunked) RT_FWD_LAUNCH(true, true);
+        else RT_FWD_LAUNCH(true, false);
+    } else {
+        if (chunked) RT_FWD_LAUNCH(false, true);
+        else RT_FWD_LAUNCH(false, false);
+    }
+#undef RT_FWD_LAUNCH
     g_launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -538,15 +594,14 @@ rt_status rt_render_batch(int32_t n, const rt_scene* const* scenes, const rt_cam
     if ((st = batch_pack(n, scenes, cams, params, outs_dev, pitches, L, &plan)) != RT_OK) return st;
     if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) || workspace_bytes < plan.table.size())
         return RT_ERR_INVALID_ARG;
-    if ((st = ensure_smem(rt_batch_kernel, plan.smem)) != RT_OK) return st;
+    if ((st = batch_smem(plan.chunked, plan.smem)) != RT_OK) return st;
     int grid = 0;
-    if ((st = batch_grid(L, plan.smem, &grid)) != RT_OK) return st;
+    if ((st = batch_grid(L, plan.smem, plan.chunked, &grid)) != RT_OK) return st;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     // pageable source: the runtime stages it before returning, so the vector may go
     cudaError_t e = cudaMemcpyAsync(workspace_dev, plan.table.data(), plan.table.size(), cudaMemcpyHostToDevice, st_);
     if (e != cudaSuccess) return cuda_status(e);
-    rt_batch_kernel<<<grid, dim3(32, (L.bx * L.by) / 32), plan.smem, st_>>>(
-        static_cast<unsigned char*>(workspace_dev), n, plan.n_items, L.staging, L.bx, L.by);
+    batch_launch(plan.chunked, grid, L, plan.smem, st_, static_cast<unsigned char*>(workspace_dev), n, plan.n_items);
     g_launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -574,15 +629,16 @@ rt_status rt_batch_create(int32_t n, const rt_scene* const* scenes, const rt_cam
     if (st != RT_OK) return st;
     BatchPlanHost plan;
     if ((st = batch_pack(n, scenes, cams, params, outs_dev, pitches, L, &plan)) != RT_OK) return st;
-    if ((st = ensure_smem(rt_batch_kernel, plan.smem)) != RT_OK) return st;
+    if ((st = batch_smem(plan.chunked, plan.smem)) != RT_OK) return st;
     rt_batch* b = new (std::nothrow) rt_batch();
     if (!b) return RT_ERR_OOM;
+    b->chunked = plan.chunked;
     b->n = n;
     b->n_items = plan.n_items;
     b->L = L;
     b->smem = plan.smem;
     b->ws_bytes = plan.table.size();
-    if ((st = batch_grid(L, plan.smem, &b->grid)) != RT_OK) {
+    if ((st = batch_grid(L, plan.smem, plan.chunked, &b->grid)) != RT_OK) {
         rt_batch_free(b);
         return st;
     }
@@ -600,8 +656,7 @@ rt_status rt_batch_create(int32_t n, const rt_scene* const* scenes, const rt_cam
     if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(b->ws, 0, sizeof(unsigned), b->cap);
-        rt_batch_kernel<<<b->grid, dim3(32, (L.bx * L.by) / 32), b->smem, b->cap>>>(
-            static_cast<unsigned char*>(b->ws), n, b->n_items, L.staging, L.bx, L.by);
+        batch_launch(b->chunked, b->grid, L, b->smem, b->cap, static_cast<unsigned char*>(b->ws), n, b->n_items);
         cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = e2;
@@ -650,29 +705,42 @@ rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_r
         return RT_ERR_INVALID_ARG;
     const int G = grad_count(s->ns, s->nl);
     const int nwarps = (L.bx * L.by) / 32;
-    const size_t stage = (sizeof(SceneHdr) + (size_t)s->ns_pad * 16 + 15) / 16 * 16;
-    const size_t smem = stage + (size_t)nwarps * G * 4;
-    if (hitrec_dev) {
-        if ((st = ensure_smem(rt_bwd_kernel<true>, smem)) != RT_OK) return st;
-    } else if ((st = ensure_smem(rt_bwd_kernel<false>, smem)) != RT_OK) {
-        return st;
-    }
+    const size_t tabs = (size_t)nwarps * G * 4;
+    const bool chunked = L.staging == 3 || stage_smem_bytes(false, s->ns_pad, nwarps) + tabs + 4096 >
+                                               (size_t)(max_smem_optin() - 1024);
+    const size_t smem = stage_smem_bytes(chunked, s->ns_pad, nwarps) + tabs;
+    const int hstage = L.staging == 2 ? 2 : 1;
     const Frame fr = make_frame(s, cam, p);
     const dim3 block(32, nwarps);
     const dim3 grid((p->width + L.bx - 1) / L.bx, (p->height + L.by - 1) / L.by);
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     float* parts = static_cast<float*>(workspace_dev);
-    if (hitrec_dev)
-        rt_bwd_kernel<true><<<grid, block, smem, st_>>>(view_of(s), fr, dl_dimg_dev, dl_pitch_bytes,
-                                                        static_cast<const float*>(hitrec_dev), parts, G, L.staging,
-                                                        L.bx, L.by);
-    else
-        rt_bwd_kernel<false><<<grid, block, smem, st_>>>(view_of(s), fr, dl_dimg_dev, dl_pitch_bytes, nullptr, parts,
-                                                         G, L.staging, L.bx, L.by);
+    const float* hr = static_cast<const float*>(hitrec_dev);
+#define RT_BWD_LAUNCH(HR, CHK)                                                                                   \
+    do {                                                                                                         \
+        if ((st = ensure_smem(rt_bwd_kernel<HR, CHK>, smem)) != RT_OK) return st;                               \
+        rt_bwd_kernel<HR, CHK><<<grid, block, smem, st_>>>(view_of(s), fr, dl_dimg_dev, dl_pitch_bytes, hr, parts, \
+                                                          G, hstage, L.bx, L.by);                               \
+    } while (0)
+    if (hr) {
+        if (chunked) RT_BWD_LAUNCH(true, true);
+        else RT_BWD_LAUNCH(true, false);
+    } else {
+        if (chunked) RT_BWD_LAUNCH(false, true);
+        else RT_BWD_LAUNCH(false, false);
+    }
+#undef RT_BWD_LAUNCH
     g_launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     rt_grad_reduce_kernel<<<(G + 255) / 256, 256, 0, st_>>>(parts, (int)(grid.x * grid.y), G, grad_dev);
+    g_launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+rt_status rt_selftest_wait_timeout(uint32_t polls, void* stream) {
+    if (polls == 0 || polls > (1u << 20)) return RT_ERR_INVALID_ARG;
+    rt_selftest_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(polls);
     g_launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -714,18 +782,21 @@ alignas(256) unsigned char g_noalloc_host[RT_NOALLOC_SCRATCH_BYTES];
 rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera* cams,
                            const rt_render_params* params, void* const* outs, const size_t* pitches,
                            const Launch& L, unsigned char* buf, size_t cap, size_t* bytes, int* n_items_out,
-                           size_t* smem_out) {
+                           size_t* smem_out, bool* chunked_out) {
     if (n < 1 || !scenes || !cams || !params || !outs || !pitches) return RT_ERR_INVALID_ARG;
     if (L.bx * L.by > kBatchMaxThreads) return RT_ERR_INVALID_ARG;
     if (n > RT_NOALLOC_MAX_FRAMES) return RT_ERR_EXCEEDS_SCRATCH;
     int order[RT_NOALLOC_MAX_FRAMES];
     int tiles[RT_NOALLOC_MAX_FRAMES];
     long long n_items = 0;
-    size_t smem = 0;
     const size_t items_off = batch_items_offset(n);
     if (items_off > cap) return RT_ERR_EXCEEDS_SCRATCH;
     std::memset(buf, 0, items_off);  // the work counter starts at zero
     BatchFrame* frames = reinterpret_cast<BatchFrame*>(buf + batch_frames_offset());
+    int max_pad = 0;
+    for (int i = 0; i < n; ++i)
+        if (scenes[i]) max_pad = std::max(max_pad, scenes[i]->ns_pad);
+    const bool chunked = use_tiled_loop(L, max_pad);
     for (int i = 0; i < n; ++i) {
         const rt_scene* s = scenes[i];
         const rt_render_params* p = &params[i];
@@ -740,13 +811,12 @@ rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera
         B.fr = make_frame(s, &cams[i], p);
         B.out = outs[i];
         B.pitch = pitches[i];
-        B.stage_bytes = (uint32_t)(sizeof(SceneHdr) + (size_t)s->ns_pad * 16);
+        B.stage_bytes = (uint32_t)(chunked ? sizeof(SceneHdr) : sizeof(SceneHdr) + (size_t)s->ns_pad * 16);
         B.tiles_x = (p->width + L.bx - 1) / L.bx;
         const long long t = (long long)B.tiles_x * ((p->height + L.by - 1) / L.by);
         if (t >= (1ll << kItemTileBits)) return RT_ERR_UNSUPPORTED;
         tiles[i] = (int)t;
         n_items += t;
-        smem = std::max(smem, (size_t)B.stage_bytes);
         // insertion into the longest-first order (stable: ties keep input order)
         const double c = tile_cost(s, p);
         int j = i;
@@ -766,7 +836,8 @@ rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera
     }
     *bytes = total;
     *n_items_out = (int)n_items;
-    *smem_out = smem;
+    *smem_out = stage_smem_bytes(chunked, max_pad, (L.bx * L.by) / 32);
+    *chunked_out = chunked;
     return RT_OK;
 }
 
@@ -792,19 +863,19 @@ extern "C" rt_status rt_render_batch_noalloc(int32_t n, const rt_scene* const* s
     }
     size_t bytes = 0, smem = 0;
     int n_items = 0;
+    bool chunked = false;
     st = batch_pack_fixed(n, scenes, cams, params, outs_dev, pitches, L, g_noalloc_host, sizeof(g_noalloc_host),
-                          &bytes, &n_items, &smem);
+                          &bytes, &n_items, &smem, &chunked);
     if (st != RT_OK) return st;
-    if ((st = ensure_smem(rt_batch_kernel, smem)) != RT_OK) return st;
+    if ((st = batch_smem(chunked, smem)) != RT_OK) return st;
     int grid = 0;
-    if ((st = batch_grid(L, smem, &grid)) != RT_OK) return st;
+    if ((st = batch_grid(L, smem, chunked, &grid)) != RT_OK) return st;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     // pageable source: staged by the runtime before the call returns, so the static
     // host image is free for the next call
     e = cudaMemcpyAsync(g_noalloc_dev_ptr[dev], g_noalloc_host, bytes, cudaMemcpyHostToDevice, st_);
     if (e != cudaSuccess) return cuda_status(e);
-    rt_batch_kernel<<<grid, dim3(32, (L.bx * L.by) / 32), smem, st_>>>(
-        static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]), n, n_items, L.staging, L.bx, L.by);
+    batch_launch(chunked, grid, L, smem, st_, static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]), n, n_items);
     g_launches++;
     return cuda_status(cudaGetLastError());
 }

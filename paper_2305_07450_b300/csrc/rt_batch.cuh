@@ -33,8 +33,9 @@ __host__ __device__ inline size_t batch_items_offset(int n) {
     return (kWsHead + (size_t)n * sizeof(BatchFrame) + 255) / 256 * 256;
 }
 
+template <bool CH>
 __global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restrict__ ws, int n_frames, int n_items,
-                                                       int staging, int block_x, int block_y) {
+                                                          int staging, int block_x, int block_y) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     __shared__ int s_item[2];
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restr
     __shared__ void* s_out;
     __shared__ size_t s_pitch;
     __shared__ int s_tiles_x;
+    __shared__ const float4* s_geo;
     __shared__ const float4* s_mat;
     __shared__ const float4* s_mat2;
     unsigned* counter = reinterpret_cast<unsigned*>(ws);
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restr
                 s_out = B->out;
                 s_pitch = B->pitch;
                 s_tiles_x = B->tiles_x;
+                s_geo = B->sv.geo;
                 s_mat = B->sv.mat;
                 s_mat2 = B->sv.mat2;
                 // shared memory was last read by the generic proxy; order those reads
@@ -83,13 +86,14 @@ __global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restr
             if (!stage_to_smem(smem, B->sv.hdr, B->stage_bytes, staging, &bar, phase, &g_err_word)) return;
             cur = fi;
         }
-        const StagedScene sc{reinterpret_cast<const SceneHdr*>(smem),
-                             reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), s_mat, s_mat2};
+        float4* tab = reinterpret_cast<float4*>(smem + sizeof(SceneHdr));
+        const StagedScene sc{reinterpret_cast<const SceneHdr*>(smem), CH ? nullptr : tab, s_geo,
+                             CH ? tab + (size_t)warp * kChunk : nullptr, s_mat, s_mat2};
         const int tx = tile % s_tiles_x, ty = tile / s_tiles_x;
         const int x = tx * block_x + (warp % wpr) * 8 + (lane & 7);
         const int y = ty * block_y + (warp / wpr) * 4 + (lane >> 3);
         const bool valid = x < s_fr.W && y < s_fr.H;
-        render_pixel<false>(sc, s_fr, x, y, valid, s_out, s_pitch, nullptr, 0);
+        render_pixel<false, CH>(sc, s_fr, x, y, valid, s_out, s_pitch, nullptr, 0);
         __syncthreads();  // every thread is done with this tile, its slot and the staged scene
         buf ^= 1;
     }

@@ -60,7 +60,7 @@ __device__ __forceinline__ void warp_group_add(float* __restrict__ wtab, int key
     }
 }
 
-template <bool FROM_HITREC>
+template <bool FROM_HITREC, bool CH>
 __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const Frame fr,
                                                      const float* __restrict__ dl, size_t dl_pitch,
                                                      const float* __restrict__ hr, float* __restrict__ partials,
@@ -73,11 +73,15 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
     if (staging == 1 && tid == 0) mbar_init(&bar, 1);
     __syncthreads();
     uint32_t phase = 0;
-    const uint32_t stage_bytes = (uint32_t)(sizeof(SceneHdr) + 16u * (uint32_t)__ldg(&sv.hdr->ns_pad));
+    const uint32_t ns_pad = (uint32_t)__ldg(&sv.hdr->ns_pad);
+    const uint32_t stage_bytes = CH ? (uint32_t)sizeof(SceneHdr) : (uint32_t)(sizeof(SceneHdr) + 16u * ns_pad);
     if (!stage_to_smem(smem, sv.hdr, stage_bytes, staging, &bar, phase, &g_err_word)) return;
     const SceneHdr& h = *reinterpret_cast<const SceneHdr*>(smem);
-    const StagedScene sc{&h, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.mat, sv.mat2};
-    float* wtabs = reinterpret_cast<float*>(smem + ((stage_bytes + 15u) & ~15u));
+    float4* tab = reinterpret_cast<float4*>(smem + sizeof(SceneHdr));
+    const uint32_t table_bytes = CH ? (uint32_t)(blockDim.y * kChunk * 16) : 16u * ns_pad;
+    const StagedScene sc{&h, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)threadIdx.y * kChunk : nullptr, sv.mat,
+                         sv.mat2};
+    float* wtabs = reinterpret_cast<float*>(smem + sizeof(SceneHdr) + table_bytes);
     float* wtab = wtabs + (size_t)warp * G;
     for (int e = lane; e < G; e += 32) wtab[e] = 0.0f;
     __syncwarp();
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
         } else {
             // recompute: the forward trace itself, recording into registers/local memory
             float loc[kMaxBounce * (2 + RT_MAX_LIGHTS)];
-            trace_pixel<true>(sc, fr, x, y, loc, 1, 0);
+            trace_pixel<true, CH>(sc, fr, x, y, loc, 1, 0);
             for (int k = 0; k <= fr.D; ++k)
                 for (int f = 0; f < 2 + nl; ++f) rec[k * kRecStride + f] = loc[k * (2 + nl) + f];
         }
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             Tt[k] = T;
             const int id = __float_as_int(rec[k * kRecStride]);
             const float t = rec[k * kRecStride + 1];
-            const HitGeom hg = hit_geometry(sc, id, o, o_lo, d, t);
+            const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t);
             float A = fr.ka;
             for (int li = 0; li < nl; ++li) {
                 const float4 Lp = h.light_p[li];
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             const int id = __float_as_int(rec[k * kRecStride]);
             const float t = rec[k * kRecStride + 1];
             const f3 d = Dd[k];
-            const HitGeom hg = hit_geometry(sc, id, Oh[k], Ol[k], d, t);
+            const HitGeom hg = hit_geometry<CH>(sc, id, Oh[k], Ol[k], d, t);
             const f3 n = hg.n;
             const f3 alb = mk3(hg.m.x, hg.m.y, hg.m.z);
             const float ks = hg.m.w, ex = hg.m2.x, rho = hg.m2.y;

@@ -8,14 +8,30 @@
 
 namespace rtd {
 
-// Staged scene as one CTA sees it: header and geometry in shared memory,
-// materials in global memory (read at hits only).
+// Staged scene as one CTA sees it: header in shared memory; the geometry table
+// either whole in shared memory (geo), or -- when it does not fit -- read chunk by
+// chunk into the warp's own slot of kChunk entries (chunk), the tiled loop; the
+// global table (geo_g) and the materials are read through the read-only cache.
+constexpr int kChunk = 64;
+
 struct StagedScene {
     const SceneHdr* hdr;   // shared
-    const float4* geo;     // shared, hdr->ns_pad entries
+    const float4* geo;     // shared, hdr->ns_pad entries (whole-table staging)
+    const float4* geo_g;   // global, hdr->ns_pad entries
+    float4* chunk;         // shared, this warp's kChunk entries (tiled loop)
     const float4* mat;     // global
     const float4* mat2;    // global
 };
+
+// Tiled loop: entries [c0, c0 + m) of the global table into the warp's slot, copied
+// by the lanes in `mask` (the lanes that run the loop), 16 bytes per lane per step.
+__device__ __forceinline__ void stage_chunk(const StagedScene& sc, unsigned mask, int c0, int m) {
+    const int lane = threadIdx.x & 31;
+    const int rank = __popc(mask & ((1u << lane) - 1u)), cnt = __popc(mask);
+    __syncwarp(mask);
+    for (int k = rank; k < m; k += cnt) sc.chunk[k] = __ldg(sc.geo_g + c0 + k);
+    __syncwarp(mask);
+}
 
 // ---------------------------------------------------------------- Section 3.2-3.3
 // NDC of pixel (x, y): the shorter side spans [-1, 1] (NDC listing of Section 3.2,
@@ -41,38 +57,53 @@ __device__ __forceinline__ f3 primary_dir(const Frame& fr, int x, int y) {
 // sqrt(disc); the near one if it is > 0, else the far one.  Spheres are taken in
 // blocks of kPad: the discriminants of a block are computed branch-free, and the
 // roots only when one of them is non-negative (one branch per block).
-__device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, float& t_out) {
-    float tb = __int_as_float(0x7f800000);  // +inf
-    int best = -1;
-    const float4* __restrict__ geo = sc.geo;
-    const int n = sc.hdr->ns_pad;
-#pragma unroll 1
-    for (int i0 = 0; i0 < n; i0 += kPad) {
-        float disc[kPad], tca[kPad];
-        float dmax = -1.0f;
+// One block of kPad spheres (at geo[0..kPad)) for the closest hit; base = index of geo[0].
+__device__ __forceinline__ void closest_block(const float4* __restrict__ geo, int base, f3 o, f3 d, float& tb,
+                                              int& best) {
+    float disc[kPad], tca[kPad];
+    float dmax = -1.0f;
+#pragma unroll
+    for (int j = 0; j < kPad; ++j) {
+        const float4 g = geo[j];
+        const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
+        tca[j] = fmaf(ocx, d.x, fmaf(ocy, d.y, ocz * d.z));
+        const float lx = fmaf(-tca[j], d.x, ocx), ly = fmaf(-tca[j], d.y, ocy), lz = fmaf(-tca[j], d.z, ocz);
+        disc[j] = fmaf(-lx, lx, fmaf(-ly, ly, fmaf(-lz, lz, g.w)));
+        dmax = fmaxf(dmax, disc[j]);
+    }
+    if (dmax >= 0.0f) {
 #pragma unroll
         for (int j = 0; j < kPad; ++j) {
-            const float4 g = geo[i0 + j];
-            const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
-            tca[j] = fmaf(ocx, d.x, fmaf(ocy, d.y, ocz * d.z));
-            const float lx = fmaf(-tca[j], d.x, ocx), ly = fmaf(-tca[j], d.y, ocy), lz = fmaf(-tca[j], d.z, ocz);
-            disc[j] = fmaf(-lx, lx, fmaf(-ly, ly, fmaf(-lz, lz, g.w)));
-            dmax = fmaxf(dmax, disc[j]);
-        }
-        if (dmax >= 0.0f) {
-#pragma unroll
-            for (int j = 0; j < kPad; ++j) {
-                if (disc[j] >= 0.0f) {
-                    const float s = __fsqrt_rn(disc[j]);
-                    float t = tca[j] - s;
-                    if (t <= 0.0f) t = tca[j] + s;
-                    if (t > 0.0f && t < tb) {
-                        tb = t;
-                        best = i0 + j;
-                    }
+            if (disc[j] >= 0.0f) {
+                const float s = __fsqrt_rn(disc[j]);
+                float t = tca[j] - s;
+                if (t <= 0.0f) t = tca[j] + s;
+                if (t > 0.0f && t < tb) {
+                    tb = t;
+                    best = base + j;
                 }
             }
         }
+    }
+}
+
+template <bool CH>
+__device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, float& t_out) {
+    float tb = __int_as_float(0x7f800000);  // +inf
+    int best = -1;
+    const int n = sc.hdr->ns_pad;
+    if constexpr (CH) {
+        const unsigned mask = __activemask();
+#pragma unroll 1
+        for (int c0 = 0; c0 < n; c0 += kChunk) {
+            const int m = min(kChunk, n - c0);
+            stage_chunk(sc, mask, c0, m);
+#pragma unroll 1
+            for (int i0 = 0; i0 < m; i0 += kPad) closest_block(sc.chunk + i0, c0 + i0, o, d, tb, best);
+        }
+    } else {
+#pragma unroll 1
+        for (int i0 = 0; i0 < n; i0 += kPad) closest_block(sc.geo + i0, i0, o, d, tb, best);
     }
     const SceneHdr& h = *sc.hdr;
     if (h.has_plane) {
@@ -101,32 +132,53 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
 // slots.  The loop runs in blocks of kPad spheres and leaves once every segment of
 // every active lane is blocked: the method's early break (Section 3.6 cast-shadows
 // listing), taken warp-wide.
+// One block of kPad spheres (at geo[0..kPad)) against R segments; returns true
+// when every segment of every lane in `mask` is blocked.
 template <int R>
+__device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, unsigned mask, f3 o,
+                                               const f3 (&dir)[4], const float (&dist)[4], bool (&occ)[4]) {
+#pragma unroll
+    for (int j = 0; j < kPad; ++j) {
+        const float4 g = geo[j];
+        const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float tca = fmaf(ocx, dir[r].x, fmaf(ocy, dir[r].y, ocz * dir[r].z));
+            const float tc = fminf(fmaxf(tca, 0.0f), dist[r]);
+            const float qx = fmaf(-tc, dir[r].x, ocx), qy = fmaf(-tc, dir[r].y, ocy), qz = fmaf(-tc, dir[r].z, ocz);
+            const float e = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, -g.w)));
+            occ[r] = occ[r] || (e < 0.0f);
+        }
+    }
+    bool done = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) done = done && occ[r];
+    return __all_sync(mask, done);
+}
+
+template <int R, bool CH>
 __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, const f3 (&dir)[4],
                                                const float (&dist)[4], bool (&occ)[4]) {
-    const float4* __restrict__ geo = sc.geo;
     const int n = sc.hdr->ns_pad;
     const unsigned mask = __activemask();
+    if constexpr (CH) {
+        bool stop = false;
 #pragma unroll 1
-    for (int i0 = 0; i0 < n; i0 += kPad) {
-#pragma unroll
-        for (int j = 0; j < kPad; ++j) {
-            const float4 g = geo[i0 + j];
-            const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float tca = fmaf(ocx, dir[r].x, fmaf(ocy, dir[r].y, ocz * dir[r].z));
-                const float tc = fminf(fmaxf(tca, 0.0f), dist[r]);
-                const float qx = fmaf(-tc, dir[r].x, ocx), qy = fmaf(-tc, dir[r].y, ocy),
-                            qz = fmaf(-tc, dir[r].z, ocz);
-                const float e = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, -g.w)));
-                occ[r] = occ[r] || (e < 0.0f);
+        for (int c0 = 0; c0 < n && !stop; c0 += kChunk) {
+            const int m = min(kChunk, n - c0);
+            stage_chunk(sc, mask, c0, m);
+#pragma unroll 1
+            for (int i0 = 0; i0 < m; i0 += kPad) {
+                if (occluded_block<R>(sc.chunk + i0, mask, o, dir, dist, occ)) {
+                    stop = true;
+                    break;
+                }
             }
         }
-        bool done = true;
-#pragma unroll
-        for (int r = 0; r < R; ++r) done = done && occ[r];
-        if (__all_sync(mask, done)) break;
+    } else {
+#pragma unroll 1
+        for (int i0 = 0; i0 < n; i0 += kPad)
+            if (occluded_block<R>(sc.geo + i0, mask, o, dir, dist, occ)) break;
     }
     const SceneHdr& h = *sc.hdr;
     if (h.has_plane) {
@@ -201,7 +253,7 @@ __device__ __forceinline__ int rays_of_light(const Frame& fr, float4 Ls) {
     return (Ls.x > 0.0f || Ls.y > 0.0f) ? fr.nsamp : 1;
 }
 
-template <bool HITREC>
+template <bool HITREC, bool CH>
 __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, f3 p,
                                               f3 p_lo, f3 n, f3 po, f3 d, float ks, float e, float* __restrict__ hr,
                                               size_t hr_k, size_t hr_plane) {
@@ -254,10 +306,10 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
             }
         }
         switch (R) {
-            case 1: occluded_group<1>(sc, po, dir, dist, occ); break;
-            case 2: occluded_group<2>(sc, po, dir, dist, occ); break;
-            case 3: occluded_group<3>(sc, po, dir, dist, occ); break;
-            default: occluded_group<4>(sc, po, dir, dist, occ); break;
+            case 1: occluded_group<1, CH>(sc, po, dir, dist, occ); break;
+            case 2: occluded_group<2, CH>(sc, po, dir, dist, occ); break;
+            case 3: occluded_group<3, CH>(sc, po, dir, dist, occ); break;
+            default: occluded_group<4, CH>(sc, po, dir, dist, occ); break;
         }
         // attribute the results to their lights in the same order
 #pragma unroll
@@ -301,11 +353,12 @@ struct HitGeom {
     float4 m, m2;   // albedo + k_s; exponent, reflectivity, r, 1/r
 };
 
+template <bool CH>
 __device__ __forceinline__ HitGeom hit_geometry(const StagedScene& sc, int id, f3 o, f3 o_lo, f3 d, float t) {
     const SceneHdr& h = *sc.hdr;
     HitGeom hg;
     if (id < h.ns) {
-        const float4 g = sc.geo[id];
+        const float4 g = CH ? __ldg(sc.geo_g + id) : sc.geo[id];
         hg.m = __ldg(sc.mat + id);
         hg.m2 = __ldg(sc.mat2 + id);
         f3 e;
@@ -352,7 +405,7 @@ __device__ __forceinline__ f3 offset_origin(const HitGeom& hg, float eps, f3& lo
 // reflection recursion of Section 3.7.1 is unrolled forward with a scalar
 // throughput: k < D adds T((1 - rho) A c + S) and sets T *= rho A; k = D adds
 // T(A c + S); a miss ends the path.  HITREC: write (id, t, vis_l) per bounce.
-template <bool HITREC>
+template <bool HITREC, bool CH>
 __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame& fr, int x, int y,
                                               float* __restrict__ hr, size_t hr_plane, size_t hr_pix) {
     const SceneHdr& h = *sc.hdr;
@@ -365,19 +418,19 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
 #pragma unroll 1
     for (; k <= fr.D; ++k) {
         float t;
-        const int id = closest_hit(sc, o, d, t);
+        const int id = closest_hit<CH>(sc, o, d, t);
         if (HITREC) {
             float* rec = hr + (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
             rec[0] = __int_as_float(id);
             rec[hr_plane] = t;
         }
         if (id < 0) break;
-        const HitGeom hg = hit_geometry(sc, id, o, o_lo, d, t);
+        const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t);
         f3 po_lo;
         const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);
         const float4 m = hg.m, m2 = hg.m2;
         const size_t hr_k = (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
-        const HitShade sh = shade_hit<HITREC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+        const HitShade sh = shade_hit<HITREC, CH>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
         const float A = sh.A, S = sh.S;
         if (k < fr.D) {
             const float w = T * (1.0f - m2.y) * A;
@@ -417,13 +470,13 @@ __device__ __forceinline__ uint32_t pack_rgba8(float3 c) {
 // Trace pixel (x, y) and store it.  All 32 lanes of the warp must call (the RGBA8
 // path gathers four horizontally adjacent pixels, lanes 4j..4j+3, into one 16-byte
 // store); `valid` marks lanes whose pixel is inside the frame.
-template <bool HITREC>
+template <bool HITREC, bool CH>
 __device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
                                              void* __restrict__ out, size_t pitch, float* __restrict__ hr,
                                              size_t hr_plane) {
     const int lane = threadIdx.x & 31;
     float3 c = make_float3(0.f, 0.f, 0.f);
-    if (valid) c = trace_pixel<HITREC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
+    if (valid) c = trace_pixel<HITREC, CH>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
     if (fr.fmt == RT_OUT_F32) {
         if (valid)
             *reinterpret_cast<float4*>(static_cast<char*>(out) + (size_t)y * pitch + (size_t)x * 16) =

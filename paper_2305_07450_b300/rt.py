@@ -83,6 +83,8 @@ def lib():
         L.rt_batch_create.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
                                       C.POINTER(sz), C.POINTER(LaunchConfig), vp, C.POINTER(vp)]
         L.rt_batch_launch.argtypes = [vp, vp]
+        L.rt_selftest_wait_timeout.argtypes = [C.c_uint32, vp]
+        L.rt_selftest_wait_timeout.restype = C.c_int
         L.rt_grad_count.argtypes = [vp]
         L.rt_grad_count.restype = sz
         L.rt_backward_workspace_bytes.argtypes = [vp, C.POINTER(RenderParams), C.POINTER(LaunchConfig)]

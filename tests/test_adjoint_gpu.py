@@ -33,14 +33,14 @@ def oracle_loss(scene, w, px, wt):
     return float((oracle.trace(scene, w.camera, w.params, px)["rgb"] * wt).sum())
 
 
-def gpu_grad(w, wimg, hitrec=True):
+def gpu_grad(w, wimg, hitrec=True, launch=None):
     ds = rt.DeviceScene(w.scene)
     p = w.params
     hr = torch.empty(rt.hitrec_bytes(ds, p) // 4 + 1, dtype=torch.float32, device="cuda") if hitrec else None
-    rt.render(ds, w.camera, p, hitrec=hr)
+    rt.render(ds, w.camera, p, hitrec=hr, launch=launch)
     dl = torch.zeros((p.height, p.width, 4), dtype=torch.float32, device="cuda")
     dl[..., :3] = torch.tensor(wimg, dtype=torch.float32, device="cuda")
-    g = rt.render_backward(ds, w.camera, p, dl, hitrec=hr)
+    g = rt.render_backward(ds, w.camera, p, dl, hitrec=hr, launch=launch)
     torch.cuda.synchronize()
     assert rt.device_errors() == 0
     ds.close()
@@ -117,6 +117,10 @@ def test_replay_equals_recompute_and_is_deterministic():
     c = gpu_grad(w, wimg, hitrec=True)
     assert np.array_equal(a, b)
     assert np.array_equal(a, c)
+    # the tiled loop (geometry staged per warp chunk) gives the same paths and sums
+    d = gpu_grad(w, wimg, hitrec=False, launch={"staging": 3})
+    e = gpu_grad(w, wimg, hitrec=True, launch={"staging": 3})
+    assert np.array_equal(a, d) and np.array_equal(a, e)
 
 
 def test_autograd_function_matches_direct_call():

@@ -46,7 +46,8 @@ def test_render_batch_workspace_path_and_staging_modes():
     ws = S.batch_scenes(12, seed0=300)
     dss = [rt.DeviceScene(w.scene) for w in ws]
     ref = per_frame(ws, dss)
-    for launch in (None, {"staging": 2}, {"block_x": 8, "block_y": 8, "min_blocks_per_sm": 1}, {"block_x": 32, "block_y": 4}):
+    for launch in (None, {"staging": 2}, {"block_x": 8, "block_y": 8, "min_blocks_per_sm": 1}, {"block_x": 32, "block_y": 4},
+                   {"staging": 3}):
         outs, _ = rt.render_batch(dss, [w.camera for w in ws], [w.params for w in ws], launch=launch)
         torch.cuda.synchronize()
         for i, (a, o) in enumerate(zip(ref, outs)):

@@ -136,9 +136,22 @@ def test_launch_shapes_and_staging_bitwise_equal():
     w.params.width, w.params.height = 200, 120
     base, _ = gpu_render(w, launch={"block_x": 16, "block_y": 16, "staging": 1})
     for cfg in ({"block_x": 16, "block_y": 16, "staging": 2}, {"block_x": 8, "block_y": 4},
-                {"block_x": 32, "block_y": 8}, {"block_x": 8, "block_y": 32}):
+                {"block_x": 32, "block_y": 8}, {"block_x": 8, "block_y": 32}, {"staging": 3},
+                {"block_x": 8, "block_y": 4, "staging": 3}):
         other, _ = gpu_render(w, launch=cfg)
         assert np.array_equal(base, other), cfg
+
+
+def test_large_scene_takes_the_tiled_loop():
+    """20000 spheres: the geometry table (320 KB) exceeds shared memory, so every
+    warp stages it chunk by chunk; parity with the oracle on a small frame."""
+    sc = S.random_scene(77, 20000, 2, 35.0)
+    w = S.Workload("20000sph", sc, S.default_camera(35.0),
+                   S._params(sc, width=48, height=32, max_depth=1, out_format=S.OUT_F32, seed=77))
+    check_f32_full(w, min_plain=0.99)
+    img_auto, _ = gpu_render(w)
+    img_forced, _ = gpu_render(w, launch={"staging": 3, "block_x": 8, "block_y": 8})
+    assert np.array_equal(img_auto, img_forced)
 
 
 def test_rgba8_is_quantised_f32():
