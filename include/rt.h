@@ -220,6 +220,17 @@ rt_status rt_render_batch_noalloc(int32_t n, const rt_scene *const *scenes, cons
                                   const rt_render_params *params, void *const *outs_dev, const size_t *pitches,
                                   const rt_launch_config *cfg, void *stream);
 
+/* Render only the rectangle [x0, x0 + width) x [y0, y0 + height) of the frame that
+ * `params` describes, into out_dev (row 0 = frame row y0, column 0 = frame column
+ * x0; same formats and pitch rules as rt_render, for `width` pixels per row).
+ * Every pixel is computed exactly as in the full frame (NDC, Philox counters and
+ * all arithmetic use frame coordinates), so bands rendered separately -- e.g. one
+ * per GPU -- stitch into the full frame bit for bit.  x0 must be a multiple of 8;
+ * no hit record. */
+rt_status rt_render_region(const rt_scene *scene, const rt_camera *cam, const rt_render_params *params,
+                           int32_t x0, int32_t y0, int32_t width, int32_t height, void *out_dev,
+                           size_t out_pitch_bytes, const rt_launch_config *cfg, void *stream);
+
 /* Bytes of the hit record of one frame: for each bounce k in 0..D and each pixel,
  * the primitive id (int32, -1 = miss), the hit distance t (float) and the visible
  * fraction of every light (float), stored plane by plane:

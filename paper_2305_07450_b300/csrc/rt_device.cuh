@@ -83,12 +83,11 @@ __host__ __device__ inline int pad_spheres(int ns) { return (ns + kPad - 1) / kP
 struct Frame {
     int W, H, D, nsamp, model, fmt;
     float ka, eps;
-    float inv_m;             // unused slot kept for alignment of the camera block
     int m;                   // min(W, H): the side the NDC square spans (Section 3.2)
+    int rx0, ry0, rx1, ry1;  // rendered region [rx0, rx1) x [ry0, ry1) of the frame
     float3 cam;              // ray origin
     float3 right, up, fwd;   // rotated camera basis; fwd already scaled by b
     uint32_t key0, key1;     // Philox key = seed
-    int vogel_n;             // = nsamp
     float sample_g_inv;      // 1 / g for the g x g stratified grid
     int sample_g;
 };

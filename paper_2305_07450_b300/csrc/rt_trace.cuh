@@ -467,9 +467,10 @@ __device__ __forceinline__ uint32_t pack_rgba8(float3 c) {
     return quant8(c.x) | (quant8(c.y) << 8) | (quant8(c.z) << 16) | 0xFF000000u;
 }
 
-// Trace pixel (x, y) and store it.  All 32 lanes of the warp must call (the RGBA8
-// path gathers four horizontally adjacent pixels, lanes 4j..4j+3, into one 16-byte
-// store); `valid` marks lanes whose pixel is inside the frame.
+// Trace pixel (x, y) of the frame and store it at (x - rx0, y - ry0) of `out`.  All
+// 32 lanes of the warp must call (the RGBA8 path gathers four horizontally adjacent
+// pixels, lanes 4j..4j+3, into one 16-byte store; rx0 is a multiple of 8); `valid`
+// marks lanes whose pixel is inside the rendered region.
 template <bool HITREC, bool CH>
 __device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
                                              void* __restrict__ out, size_t pitch, float* __restrict__ hr,
@@ -477,23 +478,24 @@ __device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame&
     const int lane = threadIdx.x & 31;
     float3 c = make_float3(0.f, 0.f, 0.f);
     if (valid) c = trace_pixel<HITREC, CH>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
+    const int lx = x - fr.rx0, ly = y - fr.ry0;
     if (fr.fmt == RT_OUT_F32) {
         if (valid)
-            *reinterpret_cast<float4*>(static_cast<char*>(out) + (size_t)y * pitch + (size_t)x * 16) =
+            *reinterpret_cast<float4*>(static_cast<char*>(out) + (size_t)ly * pitch + (size_t)lx * 16) =
                 make_float4(c.x, c.y, c.z, 1.0f);
     } else {
         const uint32_t p0 = pack_rgba8(c);
         const uint32_t p1 = __shfl_down_sync(0xffffffffu, p0, 1);
         const uint32_t p2 = __shfl_down_sync(0xffffffffu, p0, 2);
         const uint32_t p3 = __shfl_down_sync(0xffffffffu, p0, 3);
-        if ((lane & 3) == 0 && y < fr.H && x < fr.W) {
-            uint32_t* row = reinterpret_cast<uint32_t*>(static_cast<char*>(out) + (size_t)y * pitch);
-            if (x + 3 < fr.W) {
-                *reinterpret_cast<uint4*>(row + x) = make_uint4(p0, p1, p2, p3);
+        if ((lane & 3) == 0 && y < fr.ry1 && x < fr.rx1) {
+            uint32_t* row = reinterpret_cast<uint32_t*>(static_cast<char*>(out) + (size_t)ly * pitch);
+            if (x + 3 < fr.rx1) {
+                *reinterpret_cast<uint4*>(row + lx) = make_uint4(p0, p1, p2, p3);
             } else {
-                row[x] = p0;
-                if (x + 1 < fr.W) row[x + 1] = p1;
-                if (x + 2 < fr.W) row[x + 2] = p2;
+                row[lx] = p0;
+                if (x + 1 < fr.rx1) row[lx + 1] = p1;
+                if (x + 2 < fr.rx1) row[lx + 2] = p2;
             }
         }
     }

@@ -69,6 +69,9 @@ def lib():
         L.rt_scene_free.argtypes = [vp]
         L.rt_render.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), vp, sz, vp,
                                 C.POINTER(LaunchConfig), vp]
+        L.rt_render_region.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), i32, i32, i32, i32, vp, sz,
+                                       C.POINTER(LaunchConfig), vp]
+        L.rt_render_region.restype = C.c_int
         L.rt_hitrec_bytes.argtypes = [vp, C.POINTER(RenderParams)]
         L.rt_hitrec_bytes.restype = sz
         L.rt_device_errors.argtypes = [vp, C.POINTER(C.c_uint32)]
@@ -238,6 +241,26 @@ def render(dscene: DeviceScene, camera, params: scenes.Params, *, out: torch.Ten
                                        C.byref(cfg) if cfg is not None else None, _stream(stream)))
     if params.out_format != scenes.OUT_F32:
         return out[:, : params.width]
+    return out
+
+
+def render_region(dscene: DeviceScene, camera, params: scenes.Params, x0: int, y0: int, width: int, height: int,
+                  *, out: torch.Tensor | None = None, pitch: int | None = None, launch=None,
+                  stream=None) -> torch.Tensor:
+    """rt_render_region: rows y0..y0+height and columns x0..x0+width of the frame
+    described by params (x0 a multiple of 8), bit-identical to those pixels of the
+    full frame."""
+    sub = scenes.Params(**{**params.__dict__, "width": width, "height": height})
+    if out is None:
+        out, pitch = alloc_output(sub)
+    elif pitch is None:
+        pitch = out.stride(0) * out.element_size()
+    cam, prm, cfg = camera_struct(camera), params_struct(params), launch_struct(launch)
+    check("rt_render_region", lib().rt_render_region(dscene.handle, C.byref(cam), C.byref(prm), int(x0), int(y0),
+                                                     int(width), int(height), out.data_ptr(), pitch,
+                                                     C.byref(cfg) if cfg is not None else None, _stream(stream)))
+    if params.out_format != scenes.OUT_F32:
+        return out[:, :width]
     return out
 
 

@@ -196,3 +196,20 @@ def test_hitrec_primary_hits_match_oracle():
 def test_device_error_word_clear_after_renders():
     gpu_render(S.whitted_256())
     assert rt.device_errors() == 0
+
+
+def test_region_bands_stitch_bit_identical():
+    """Row bands and an interior rectangle rendered by rt_render_region equal the
+    same pixels of the full frame (RGBA8 and F32), as used to split a frame over
+    GPUs."""
+    from paper_2305_07450_b300 import shard
+    for fmt in (S.OUT_RGBA8, S.OUT_F32):
+        w = S.area_4k()
+        w.params.width, w.params.height, w.params.out_format = 640, 360, fmt
+        ds = rt.DeviceScene(w.scene)
+        full = rt.render(ds, w.camera, w.params).cpu().numpy()
+        parts = [shard.render_band(ds, w.camera, w.params, a, b).cpu().numpy()
+                 for a, b in shard.row_bands(w.params.height, 3)]
+        assert np.array_equal(np.concatenate(parts, 0), full)
+        sub = rt.render_region(ds, w.camera, w.params, 104, 50, 203, 77).cpu().numpy()
+        assert np.array_equal(sub, full[50:127, 104:307])
