@@ -364,7 +364,35 @@ def extras(args, dev, stream):
     for d in dss:
         d.close()
     out["fwd_adjoint"] = fwd_adjoint(dev, stream)
+    out["paper_scene"] = paper_scene(dev, stream)
     return out
+
+
+PAPER_FPS_RTX2060 = {"1280x720": 234, "1920x1080": 152, "3840x2160": 45}
+
+
+def paper_scene(dev, stream):
+    """The paper's benchmark-scene structure (one spherical light, one plane, five
+    spheres; seeded, no sky): its real-time settings (hard shadows = 1 sample,
+    bounce limit 1) and its render-only settings (200 sunflower samples, bounce
+    limit 3) at 720p / 1080p / 4K, and the sweeps of its Section 4.3 (shadow
+    samples at bounce 1; bounce limit at 200 samples), frames/s on this GPU."""
+    from paper_2305_07450_b300 import rt
+
+    def fps(w):
+        ds = rt.DeviceScene(w.scene)
+        o, pitch = rt.alloc_output(w.params, device=dev)
+        ms = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o, pitch=pitch, stream=stream), stream, 10)
+        ds.close()
+        return 1e3 / ms
+    res = {"note": "paper's figures (RTX 2060, GUI, its own scene with HDR sky) are context, not a target",
+           "paper_reported_fps_hard_b1": PAPER_FPS_RTX2060}
+    for tag, samples, depth in (("hard_b1", 1, 1), ("soft200_b3", 200, 3)):
+        res[tag] = {f"{W}x{H}": fps(S.paper_scene(W, H, samples, depth))
+                    for W, H in ((1280, 720), (1920, 1080), (3840, 2160))}
+    res["samples_sweep_1280x720_b1"] = {n: fps(S.paper_scene(1280, 720, n, 1)) for n in (1, 10, 50, 100, 200, 300, 500)}
+    res["bounce_sweep_1280x720_s200"] = {d: fps(S.paper_scene(1280, 720, 200, d)) for d in range(0, 9)}
+    return res
 
 
 def fwd_adjoint(dev, stream):

@@ -101,6 +101,10 @@ typedef struct {
                                  (float RGBA, A = 1, linear, not clamped)             */
     float ambient;            /* ambient strength k_a in [0, 1] (Section 3.5.1)        */
     float eps;                /* offset of secondary ray origins along the normal     */
+    int32_t refl_coupled;     /* 0: reflection ratio = the reflectivity field;  1: the
+                                 paper's coupling (Section 3.7): ratio = spec_exp /
+                                 max_reflectivity, clamped to 1 (forward only)        */
+    float max_reflectivity;   /* MAX_REFLECTIVITY of the coupling (> 0 when coupled)   */
     uint64_t seed;            /* Philox4x32-10 key of the area-light samples           */
 } rt_render_params;
 

@@ -42,7 +42,8 @@ class OrcIn(C.Structure):
         ("width", C.c_int), ("height", C.c_int), ("max_depth", C.c_int),
         ("shadow_samples", C.c_int), ("shading_model", C.c_int), ("pad_", C.c_int),
         ("ambient", C.c_double), ("eps", C.c_double), ("scene_scale", C.c_double),
-        ("seed", C.c_uint64),
+        ("seed", C.c_uint64), ("refl_coupled", C.c_int), ("pad2_", C.c_int),
+        ("max_reflectivity", C.c_double),
     ]
 
 
@@ -115,6 +116,8 @@ class _In:
         s.eps = float(params.eps)
         s.scene_scale = float(scene.scene_scale)
         s.seed = int(params.seed) & 0xFFFFFFFFFFFFFFFF
+        s.refl_coupled = int(getattr(params, "refl_coupled", 0))
+        s.max_reflectivity = float(getattr(params, "max_reflectivity", 0.0))
         self.s = s
 
 

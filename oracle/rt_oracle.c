@@ -55,6 +55,9 @@ typedef struct {
     double eps;             /* absolute offset of secondary ray origins            */
     double scene_scale;     /* length unit of the margins                          */
     uint64_t seed;          /* Philox key                                          */
+    int refl_coupled;       /* 1: reflection ratio = spec_exp / max_reflectivity   */
+    int pad2_;
+    double max_reflectivity;
 } orc_in;
 
 /* One primitive promoted to FP64.  For the plane, g = normal and r = d. */
@@ -494,6 +497,7 @@ static void trace_forward(Path *P, v3 o, v3 d, double out[3])
 static int build_ctx(const orc_in *in, Ctx *cx)
 {
     if (!in || in->width <= 0 || in->height <= 0 || in->max_depth < 0 || in->n_spheres < 0
+        || (in->refl_coupled && !(in->max_reflectivity > 0.0))
         || in->n_lights < 0 || !in->camera || (in->n_spheres && !in->spheres)
         || (in->n_lights && !in->lights) || (in->has_plane && !in->plane))
         return -1;
@@ -511,6 +515,10 @@ static int build_ctx(const orc_in *in, Ctx *cx)
         p->r = f[3];
         p->alb[0] = f[4]; p->alb[1] = f[5]; p->alb[2] = f[6];
         p->ks = f[7]; p->ex = f[8]; p->rho = f[9];
+        /* Section 3.7: the paper derives the reflection ratio from the same
+         * reflectivity value that is the Phong exponent, divided by
+         * MAX_REFLECTIVITY (a fully reflective mirror at the maximum). */
+        if (in->refl_coupled) p->rho = fmin(p->ex / in->max_reflectivity, 1.0);
     }
     int sampled = 0;
     for (int l = 0; l < cx->nl; ++l) {

@@ -224,6 +224,8 @@ rt_status validate_params(const rt_scene* s, const rt_render_params* p) {
     if (p->shading_model != RT_PHONG && p->shading_model != RT_BLINN_PHONG) return RT_ERR_INVALID_ARG;
     if (p->out_format != RT_OUT_RGBA8 && p->out_format != RT_OUT_F32) return RT_ERR_INVALID_ARG;
     if (!std::isfinite(p->ambient) || !std::isfinite(p->eps) || p->eps < 0.f) return RT_ERR_INVALID_ARG;
+    if (p->refl_coupled != 0 && p->refl_coupled != 1) return RT_ERR_INVALID_ARG;
+    if (p->refl_coupled && !(p->max_reflectivity > 0.f && std::isfinite(p->max_reflectivity))) return RT_ERR_INVALID_ARG;
     if (s->any_area) {
         const int g = (int)std::lround(std::sqrt((double)p->shadow_samples));
         if (g * g != p->shadow_samples) return RT_ERR_INVALID_ARG;
@@ -261,6 +263,7 @@ Frame make_frame(const rt_scene* s, const rt_camera* c, const rt_render_params* 
     fr.fwd = make_float3((float)(b * cp * sy), (float)(b * sp), (float)(b * cp * cy));
     fr.key0 = (uint32_t)(p->seed & 0xffffffffu);
     fr.key1 = (uint32_t)(p->seed >> 32);
+    fr.refl_inv_max = p->refl_coupled ? (float)(1.0 / (double)p->max_reflectivity) : 0.0f;
     fr.rx0 = 0;
     fr.ry0 = 0;
     fr.rx1 = p->width;
@@ -719,6 +722,7 @@ rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_r
     rt_status st = validate_params(s, p);
     if (st != RT_OK) return st;
     if ((st = validate_camera(cam)) != RT_OK) return st;
+    if (p->refl_coupled) return RT_ERR_UNSUPPORTED;
     if (!dl_dimg_dev || (reinterpret_cast<uintptr_t>(dl_dimg_dev) & 15) || dl_pitch_bytes < (size_t)p->width * 16 ||
         (dl_pitch_bytes & 15) || !grad_dev || (hitrec_dev && (reinterpret_cast<uintptr_t>(hitrec_dev) & 3)))
         return RT_ERR_INVALID_ARG;

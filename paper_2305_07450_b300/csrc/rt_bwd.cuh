@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             Tt[k] = T;
             const int id = __float_as_int(rec[k * kRecStride]);
             const float t = rec[k * kRecStride + 1];
-            const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t);
+            const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t, 0.0f);
             float A = fr.ka;
             for (int li = 0; li < nl; ++li) {
                 const float4 Lp = h.light_p[li];
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             const int id = __float_as_int(rec[k * kRecStride]);
             const float t = rec[k * kRecStride + 1];
             const f3 d = Dd[k];
-            const HitGeom hg = hit_geometry<CH>(sc, id, Oh[k], Ol[k], d, t);
+            const HitGeom hg = hit_geometry<CH>(sc, id, Oh[k], Ol[k], d, t, 0.0f);
             const f3 n = hg.n;
             const f3 alb = mk3(hg.m.x, hg.m.y, hg.m.z);
             const float ks = hg.m.w, ex = hg.m2.x, rho = hg.m2.y;

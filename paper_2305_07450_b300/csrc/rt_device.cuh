@@ -90,6 +90,7 @@ struct Frame {
     uint32_t key0, key1;     // Philox key = seed
     float sample_g_inv;      // 1 / g for the g x g stratified grid
     int sample_g;
+    float refl_inv_max;      // > 0: reflection ratio = min(spec_exp * refl_inv_max, 1)
 };
 
 // ------------------------------------------------------------------ Philox4x32-10

@@ -354,7 +354,8 @@ struct HitGeom {
 };
 
 template <bool CH>
-__device__ __forceinline__ HitGeom hit_geometry(const StagedScene& sc, int id, f3 o, f3 o_lo, f3 d, float t) {
+__device__ __forceinline__ HitGeom hit_geometry(const StagedScene& sc, int id, f3 o, f3 o_lo, f3 d, float t,
+                                                float refl_inv_max) {
     const SceneHdr& h = *sc.hdr;
     HitGeom hg;
     if (id < h.ns) {
@@ -381,6 +382,8 @@ __device__ __forceinline__ HitGeom hit_geometry(const StagedScene& sc, int id, f
         hg.p_lo = add(e, o_lo);
         hg.n = xyz(h.plane_g);
     }
+    // the paper's coupling of reflection ratio and specular exponent (Section 3.7)
+    if (refl_inv_max > 0.0f) hg.m2.y = fminf(hg.m2.x * refl_inv_max, 1.0f);
     hg.flip = 1.0f;
     if (dot(hg.n, d) > 0.0f) {
         hg.n = scl(hg.n, -1.0f);
@@ -425,7 +428,7 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
             rec[hr_plane] = t;
         }
         if (id < 0) break;
-        const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t);
+        const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t, fr.refl_inv_max);
         f3 po_lo;
         const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);
         const float4 m = hg.m, m2 = hg.m2;

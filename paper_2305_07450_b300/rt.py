@@ -40,7 +40,7 @@ class RenderParams(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("max_depth", C.c_int32),
                 ("shadow_samples", C.c_int32), ("shading_model", C.c_int32),
                 ("out_format", C.c_int32), ("ambient", C.c_float), ("eps", C.c_float),
-                ("seed", C.c_uint64)]
+                ("refl_coupled", C.c_int32), ("max_reflectivity", C.c_float), ("seed", C.c_uint64)]
 
 
 class LaunchConfig(C.Structure):
@@ -131,6 +131,7 @@ def params_struct(p: scenes.Params) -> RenderParams:
     s.width, s.height, s.max_depth = int(p.width), int(p.height), int(p.max_depth)
     s.shadow_samples, s.shading_model, s.out_format = int(p.shadow_samples), int(p.shading_model), int(p.out_format)
     s.ambient, s.eps = float(p.ambient), float(p.eps)
+    s.refl_coupled, s.max_reflectivity = int(p.refl_coupled), float(p.max_reflectivity)
     s.seed = int(p.seed) & 0xFFFFFFFFFFFFFFFF
     return s
 

@@ -80,6 +80,8 @@ class Params:
     ambient: float = AMBIENT
     eps: float = EPS_SCALE * 5.0   # absolute self-intersection offset
     seed: int = 0
+    refl_coupled: int = 0          # 1: reflection ratio = spec_exp / max_reflectivity (Section 3.7)
+    max_reflectivity: float = 0.0
 
 
 @dataclasses.dataclass
@@ -180,6 +182,23 @@ def area_scene_1080p() -> Workload:
     w.name = "1920x1080_256sph_3pt1area16_d8_rgba8"
     w.params.width, w.params.height = 1920, 1080
     return w
+
+
+def paper_scene(width: int = 1280, height: int = 720, samples: int = 1, depth: int = 1,
+                light_radius: float = 0.5) -> Workload:
+    """The structure of the paper's benchmark scene (Section 4.1: one light, one
+    plane, five spheres; its coordinates and HDR sky are not given): seeded, s = 1,
+    one spherical light sampled with `samples` sunflower points (Section 3.6.1; 1
+    sample = the light's centre, a hard shadow), reflection bounce limit `depth`,
+    Blinn-Phong shading (the paper's final model, Section 3.5.2).  The paper's
+    real-time figures use samples 1 / depth 1, its render-only speed-up samples
+    200 / depth 3 (Section 4)."""
+    sc = random_scene(2305, 5, 1, 1.0)
+    sc.lights[:, 5] = light_radius
+    name = f"paper_{width}x{height}_5sph_1sphlight_s{samples}_d{depth}_rgba8"
+    return Workload(name, sc, default_camera(1.0),
+                    _params(sc, width=width, height=height, max_depth=depth, shadow_samples=samples,
+                            shading_model=BLINN_PHONG, out_format=OUT_RGBA8, seed=2305))
 
 
 BATCH_RESOLUTIONS = ((256, 256), (640, 480), (1280, 720), (1920, 1080))

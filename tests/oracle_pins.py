@@ -435,6 +435,27 @@ def pin_reflection_mixing_closed_form(orc):
         assert np.allclose(got, want, atol=1e-12), (D, got, want)
 
 
+def pin_coupled_reflectivity(orc):
+    """Section 3.7: with the paper's coupling the reflection ratio is the Phong
+    exponent / MAX_REFLECTIVITY (capped at a mirror); the reflectivity field is
+    then unused.  Same closed form as the depth-1 mixing pin, with exponents 16 and
+    48 over MAX_REFLECTIVITY 64 (ratios 1/4 and 3/4)."""
+    cp = np.array([f32(v) for v in (0.9, 0.5, 0.1)])
+    cs = np.array([f32(v) for v in (0.2, 0.7, 0.4)])
+    ka = f32(0.5)
+    sc, cam, p = mk(spheres=[sphere((0, 10, 0), 2.0, albedo=tuple(cs), ex=48.0, refl=0.01)],
+                    plane=plane_rec(albedo=tuple(cp), ex=16.0, refl=0.99),
+                    camera=(0, 5, 0, 0, -90, 60), W=4, H=4, D=2, ka=ka)
+    p.refl_coupled, p.max_reflectivity = 1, 64.0
+    rp, rs = 0.25, 0.75
+    want = ka * ((1 - rp) * cp + rp * ka * ((1 - rs) * cs + rs * ka * cp))
+    got = pix(orc, sc, cam, p, 2, 2)
+    assert np.allclose(got, want, atol=1e-12), (got, want)
+    p.max_reflectivity = 8.0       # both ratios capped at 1: pure mirrors below the last bounce
+    want = ka * (ka * (ka * cp))
+    assert np.allclose(pix(orc, sc, cam, p, 2, 2), want, atol=1e-12)
+
+
 def pin_recursion_equals_loop(orc, n_scenes=2000):
     """Section 3.7.1 vs 3.7.2: the literal recursion and the forward loop agree on
     thousands of random 8x8 scenes (hard, area-light and Blinn variants)."""

@@ -148,3 +148,12 @@ def test_inverse_rendering_reduces_loss_and_parameter_error(tmp_path):
     # resume from the checkpoint: continues where it stopped
     out2 = inverse.inverse_render(w, tgt, steps=110, lr=0.05, checkpoint=str(tmp_path / "ck.pt"))
     assert len(out2["history"]) == 110 and out2["history"][99] == h[99]
+
+
+def test_backward_refuses_the_coupled_mode():
+    w = small_diff_workload(32, 32)
+    w.params.refl_coupled, w.params.max_reflectivity = 1, 64.0
+    ds = rt.DeviceScene(w.scene)
+    dl = torch.zeros((32, 32, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(rt.RtError):
+        rt.render_backward(ds, w.camera, w.params, dl)

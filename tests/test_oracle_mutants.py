@@ -16,7 +16,7 @@ ORDER = ["pin_ndc_worked_example", "pin_ndc_shorter_side_spans_unit_square",
          "pin_ties_lowest_index", "pin_phong_closed_forms", "pin_single_sphere_lit_side", "pin_blinn_closed_form",
          "pin_plane_horizon", "pin_occlusion_invariant", "pin_philox_kat", "pin_rgba8",
          "pin_margin_grazing", "pin_counters", "pin_area_samples_stratified", "pin_vogel_sunflower",
-         "pin_reflection_mixing_closed_form",
+         "pin_reflection_mixing_closed_form", "pin_coupled_reflectivity",
          "pin_depth_reductions", "pin_area_light", "pin_mirror_symmetry",
          "pin_recursion_equals_loop", "pin_occlusion_brute_force",
          "pin_closest_hit_brute_force"]
@@ -61,6 +61,7 @@ MUTANTS = {
     "vogel_double_radius": ("double r = L->srad * sqrt((double)i / (double)n);",
                             "double r = 2.0 * L->srad * sqrt((double)i / (double)n);"),
     "vogel_angle": ("double phi = M_PI * (3.0 - sqrt(5.0));", "double phi = M_PI * (3.0 - sqrt(3.0));"),
+    "coupled_uncapped": ("p->rho = fmin(p->ex / in->max_reflectivity, 1.0);", "p->rho = p->ex / in->max_reflectivity;"),
 }
 
 

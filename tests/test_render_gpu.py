@@ -71,7 +71,11 @@ def small_cases():
         "sphere_light": mk(spheres=sph, plane=plane_rec(refl=0.25), lights=[light((0, 6, 0), 0.9, srad=0.7)],
                            camera=cam, W=48, H=32, D=1, samples=20),
         "no_plane_deep": mk(spheres=sph, lights=lig, camera=cam, W=32, H=32, D=8),
+        "coupled_reflectivity": mk(spheres=sph, plane=plane_rec(refl=0.25), lights=lig, camera=cam, W=40, H=32,
+                                   D=3, model=S.BLINN_PHONG),
     }
+    cases["coupled_reflectivity"][2].refl_coupled = 1
+    cases["coupled_reflectivity"][2].max_reflectivity = 64.0
     return cases
 
 
@@ -213,3 +217,11 @@ def test_region_bands_stitch_bit_identical():
         assert np.array_equal(np.concatenate(parts, 0), full)
         sub = rt.render_region(ds, w.camera, w.params, 104, 50, 203, 77).cpu().numpy()
         assert np.array_equal(sub, full[50:127, 104:307])
+
+
+@pytest.mark.parametrize("samples,depth", [(1, 1), (200, 3)])
+def test_paper_scene_soft_shadows(samples, depth):
+    """The paper's scene structure with its two settings: hard shadows (1 sample)
+    at bounce 1, and 200 sunflower samples at bounce 3 (Sections 3.6.1, 4)."""
+    w = S.paper_scene(128, 72, samples, depth)
+    check_f32_full(w, min_plain=0.995)
