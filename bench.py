@@ -363,9 +363,48 @@ def extras(args, dev, stream):
     b.close()
     for d in dss:
         d.close()
+    out["bvh"] = bvh_extra(dev, stream)
     out["fwd_adjoint"] = fwd_adjoint(dev, stream)
     out["paper_scene"] = paper_scene(dev, stream)
     return out
+
+
+def bvh_extra(dev, stream):
+    """The sphere hierarchy (the paper's future work; not the headline, which is
+    the paper's brute-force method): frames/s through it against brute force on
+    the 4K workload, the 1080p area-light scene and a 4096-sphere scene, with the
+    outputs compared bit for bit on the device."""
+    import torch
+    from paper_2305_07450_b300 import autotune, rt
+    big = S.random_scene(41, 4096, 2, 12.0, area_lights=1)
+    cases = [workload("4k"), workload("4k_scene_1080p"),
+             S.Workload("1920x1080_4096sph_2pt+area16_d4_rgba8", big, S.default_camera(12.0),
+                        S._params(big, width=1920, height=1080, max_depth=4, shadow_samples=16, seed=41))]
+    res = {}
+    for w in cases:
+        ds = rt.DeviceScene(w.scene)
+        info = ds.build_bvh(stream=stream)
+        o1, pitch = rt.alloc_output(w.params, device=dev)
+        o2, _ = rt.alloc_output(w.params, device=dev)
+        bf = autotune.tune_render(ds, w.scene, w.camera, w.params, stream=stream)
+        ms_bf = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o1, pitch=pitch, launch=bf, stream=stream),
+                             stream, 5)
+        best = None
+        for cand in ({"block_x": 16, "block_y": 8}, {"block_x": 8, "block_y": 8}, {"block_x": 32, "block_y": 4},
+                     {"block_x": 8, "block_y": 16}, {"block_x": 16, "block_y": 16}):
+            cfg = dict(cand, accel=1, staging=1)
+            ms = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o2, pitch=pitch, launch=cfg,
+                                                stream=stream), stream, 5)
+            if best is None or ms < best[0]:
+                best = (ms, cfg)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(o1, o2))
+        res[w.name] = {"spheres": w.scene.n_spheres, "hierarchy": info, "ms_brute_force": ms_bf,
+                       "ms_bvh": best[0], "launch_bvh": best[1], "frames_per_s_brute_force": 1e3 / ms_bf,
+                       "frames_per_s_bvh": 1e3 / best[0], "speedup": ms_bf / best[0], "bit_identical": same}
+        ds.close()
+    assert rt.device_errors() == 0
+    return res
 
 
 PAPER_FPS_RTX2060 = {"1280x720": 234, "1920x1080": 152, "3840x2160": 45}

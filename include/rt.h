@@ -111,12 +111,17 @@ typedef struct {
 /* Launch shape of the render kernels.  A zeroed struct (or NULL) means "library
  * default".  Threads of a CTA form block_x * block_y pixels; each warp covers an
  * 8 x 4 pixel patch.  staging: 0 = default, 1 = one TMA bulk copy of the scene
- * table into shared memory, 2 = cooperative copy by all threads (same results
- * bit for bit). */
+ * table into shared memory, 2 = cooperative copy by all threads, 3 = the tiled
+ * loop (each warp streams the sphere table through its own shared-memory slot;
+ * taken anyway when the table does not fit).  accel: 0 = brute force over the
+ * spheres (the paper's method), 1 = the scene's bounding-volume hierarchy
+ * (rt_scene_build_bvh; rt_render and rt_render_region only, staging 1 or 2).
+ * Every choice gives the same results bit for bit. */
 typedef struct {
     int32_t block_x, block_y; /* multiples of 8 and 4, block_x * block_y in 32..256 */
     int32_t staging;
     int32_t min_blocks_per_sm;/* occupancy hint for the batch kernel's grid size     */
+    int32_t accel;            /* 0 brute force, 1 bounding-volume hierarchy          */
 } rt_launch_config;
 
 typedef struct rt_scene rt_scene;   /* opaque, device-resident */
@@ -140,9 +145,45 @@ rt_status rt_scene_update(rt_scene *scene, const rt_scene_desc *desc, int32_t de
  * NULL is accepted. */
 rt_status rt_scene_free(rt_scene *scene);
 
+/* ---------------------------------------------------------------- hierarchy
+ * Bounding-volume hierarchy over the spheres: the spatial acceleration structure
+ * the paper names as future work (Section 6); the paper's own kernel tests every
+ * sphere (Section 3.4.1).  Rendering with it (rt_launch_config.accel = 1) gives
+ * the brute-force images bit for bit: the same per-sphere arithmetic, ties to the
+ * lower index, and boxes widened per ray beyond the FP32 error of both tests.
+ * Built on the host by binned surface-area splits (leaves of at most 8 spheres,
+ * depth at most 44), from the sphere table as the device holds it. */
+typedef struct {
+    int32_t n_nodes;          /* interior nodes (64 bytes each); 0 for no spheres   */
+    int32_t depth;            /* deepest leaf (root = 0)                           */
+    int32_t max_leaf;         /* most spheres in one leaf                          */
+    float r_scene;            /* max over spheres of max(|cx|, |cy|, |cz|) + r     */
+} rt_bvh_info;
+
+/* Build (or rebuild) the scene's hierarchy from the contents last given on the
+ * host (rt_scene_upload or a host-side rt_scene_update) and enqueue its copy to
+ * the device on `stream`.  A host-side rt_scene_update of a scene that has a
+ * hierarchy rebuilds it; a device-side update (desc_on_device) leaves it stale,
+ * and accel renders then return RT_ERR_UNSUPPORTED until a host-side update.
+ * Scenes whose coordinates reach 1e15 are refused (RT_ERR_UNSUPPORTED).
+ * info (nullable) receives the hierarchy's figures. */
+rt_status rt_scene_build_bvh(rt_scene *scene, void *stream, rt_bvh_info *info);
+
+/* Host-only build of the same hierarchy for inspection (no device, no CUDA call):
+ * the records of `desc` as rt_scene_upload takes them (validated the same way).
+ *   nodes:    NULL, or room for nodes_cap 64-byte nodes: for each node the two
+ *             children's boxes as floats (a.lo xyz, a.hi xyz, b.lo xyz, b.hi xyz)
+ *             then int32 references a, b and two zero words; a reference r >= 0
+ *             is node r, r < 0 a leaf of the (((-1 - r) & 15) + 1) spheres listed
+ *             at prim_idx[(-1 - r) >> 4 ...]; an empty child has lo > hi.
+ *   prim_idx: NULL, or room for n_spheres int32 sphere indices.
+ * RT_ERR_INVALID_ARG when nodes_cap is below the node count (reported in info). */
+rt_status rt_bvh_build_host(const rt_scene_desc *desc, void *nodes, int32_t nodes_cap, int32_t *prim_idx,
+                            rt_bvh_info *info);
+
 /* Render one frame: for every pixel (x, y) a primary ray through its NDC point
  * (Section 3.2, 3.3), the closest of all primitives by brute force (Section
- * 3.4.1), ambient + per-light diffuse and specular shading with hard or sampled
+ * 3.4.1; or through the hierarchy when cfg->accel = 1, same result), ambient + per-light diffuse and specular shading with hard or sampled
  * shadows (Sections 3.5, 3.6), reflection bounces to depth D (Section 3.7) and the
  * colour written to the framebuffer (Section 3.9 render listing).
  *   out_dev: device buffer of `height` rows, `out_pitch_bytes` apart (a multiple
@@ -276,7 +317,8 @@ rt_status rt_render_backward(const rt_scene *scene, const rt_camera *cam, const 
                              const rt_launch_config *cfg, void *stream);
 
 /* Read and clear the device error word (bit 0: a shared-memory staging wait gave
- * up; bit 1: a batch work-queue wait gave up).  Synchronises `stream`.  Returns
+ * up; bit 1: a batch work-queue wait gave up; bit 2: a hierarchy traversal stack
+ * would have overflowed).  Synchronises `stream`.  Returns
  * RT_ERR_TIMEOUT when a bit was set, RT_OK otherwise; *bits (nullable) receives
  * the word. */
 rt_status rt_device_errors(void *stream, uint32_t *bits);

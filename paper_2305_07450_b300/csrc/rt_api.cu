@@ -14,6 +14,8 @@
 
 #include "../../include/rt.h"
 #include "rt_batch.cuh"
+#include "rt_bvh.cuh"
+#include "rt_bvh_build.h"
 #include "rt_bwd.cuh"
 #include "rt_device.cuh"
 #include "rt_errword.cuh"
@@ -32,6 +34,15 @@ struct rt_scene {
     void* pinned = nullptr;  // host staging of the blob
     cudaEvent_t copy_done = nullptr;
     int device = 0;
+    // the pinned blob holds the device contents (false after a device-side update)
+    bool host_current = true;
+    // hierarchy: 0 none, 1 current, 2 stale (device-side update since the build)
+    int bvh_state = 0;
+    void* bvh_dev = nullptr;     // [nodes][prim_idx], room for the most nodes ns can need
+    void* bvh_pinned = nullptr;
+    size_t bvh_cap = 0;
+    cudaEvent_t bvh_copy_done = nullptr;
+    rt_bvh_info bvh_info{};
 };
 
 static SceneView view_of(const rt_scene* s) {
@@ -75,6 +86,44 @@ __global__ void __maxnreg__(96) rt_fwd_kernel(const SceneView sv, const Frame fr
     const int y = fr.ry0 + blockIdx.y * block_y + (warp / wpr) * 4 + (lane >> 3);
     const bool valid = x < fr.rx1 && y < fr.ry1;
     render_pixel<HITREC, CH>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
+}
+
+// Forward kernel over the sphere hierarchy: the same pixels as rt_fwd_kernel, the
+// closest hit and the shadow segments taken through the hierarchy.  When
+// bvh_stage_bytes != 0 the geometry table and the hierarchy are staged in shared
+// memory after the header (two copies on the same barrier); otherwise both are
+// read from global memory through the caches.
+template <bool HITREC>
+__global__ void __launch_bounds__(256) rt_fwd_bvh_kernel(const SceneView sv, const BvhView bv,
+                                                         uint32_t bvh_stage_bytes, const Frame fr,
+                                                         void* __restrict__ out, size_t pitch, float* __restrict__ hr,
+                                                         size_t hr_plane, int staging, int block_x, int block_y) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (staging == 1 && tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const bool staged = bvh_stage_bytes != 0;
+    const uint32_t geo_bytes = staged ? 16u * (uint32_t)__ldg(&sv.hdr->ns_pad) : 0u;
+    if (!stage_to_smem(smem, sv.hdr, (uint32_t)sizeof(SceneHdr) + geo_bytes, staging, &bar, phase, &g_err_word))
+        return;
+    unsigned char* bvh_s = smem + sizeof(SceneHdr) + geo_bytes;
+    if (staged && !stage_to_smem(bvh_s, bv.nodes, bvh_stage_bytes, staging, &bar, phase, &g_err_word)) return;
+    const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
+    StagedScene sc{hdr, staged ? reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)) : sv.geo, sv.geo, nullptr,
+                   sv.mat, sv.mat2};
+    sc.bvh = bv;
+    if (staged) {
+        sc.bvh.nodes = reinterpret_cast<const BvhNode*>(bvh_s);
+        sc.bvh.prim = reinterpret_cast<const int32_t*>(bvh_s + (size_t)bv.n_nodes * sizeof(BvhNode));
+    }
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int wpr = block_x >> 3;
+    const int x = fr.rx0 + blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
+    const int y = fr.ry0 + blockIdx.y * block_y + (warp / wpr) * 4 + (lane >> 3);
+    const bool valid = x < fr.rx1 && y < fr.ry1;
+    render_pixel<HITREC, false, true>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
 }
 
 // Failure-detection self-test: the barrier expects bytes that no copy will ever
@@ -275,8 +324,12 @@ Frame make_frame(const rt_scene* s, const rt_camera* c, const rt_render_params* 
     return fr;
 }
 
+// Coordinates at or above this are refused by the hierarchy (its per-ray box
+// widening and the slab products stay far from FP32 overflow below it).
+constexpr double kBvhCoordLimit = 1e15;
+
 struct Launch {
-    int bx, by, staging, min_blocks;
+    int bx, by, staging, min_blocks, accel;
 };
 
 rt_status resolve_launch(const rt_launch_config* cfg, Launch* L) {
@@ -284,16 +337,20 @@ rt_status resolve_launch(const rt_launch_config* cfg, Launch* L) {
     L->by = 8;
     L->staging = 1;
     L->min_blocks = 0;
+    L->accel = 0;
     if (cfg) {
         if (cfg->block_x) L->bx = cfg->block_x;
         if (cfg->block_y) L->by = cfg->block_y;
         if (cfg->staging) L->staging = cfg->staging;
         if (cfg->min_blocks_per_sm < 0 || cfg->min_blocks_per_sm > 32) return RT_ERR_INVALID_ARG;
         L->min_blocks = cfg->min_blocks_per_sm;
+        if (cfg->accel < 0 || cfg->accel > 1) return RT_ERR_INVALID_ARG;
+        L->accel = cfg->accel;
     }
     if (L->bx % 8 || L->by % 4 || L->bx < 8 || L->by < 4 || L->bx * L->by < 32 || L->bx * L->by > 256)
         return RT_ERR_INVALID_ARG;
     if (L->staging < 1 || L->staging > 3) return RT_ERR_INVALID_ARG;
+    if (L->accel && L->staging == 3) return RT_ERR_INVALID_ARG;
     return RT_OK;
 }
 
@@ -349,6 +406,7 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
     if (n < 1 || n > (1 << (32 - kItemTileBits)) || !scenes || !cams || !params || !outs || !pitches)
         return RT_ERR_INVALID_ARG;
     if (L.bx * L.by > kBatchMaxThreads) return RT_ERR_INVALID_ARG;
+    if (L.accel) return RT_ERR_UNSUPPORTED;
     std::vector<BatchFrame> frames((size_t)n);
     std::vector<int> tiles((size_t)n);
     long long n_items = 0;
@@ -462,6 +520,88 @@ const char* rt_status_string(rt_status s) {
 
 uint64_t rt_launch_count(void) { return g_launches.load(); }
 
+}  // extern "C"
+
+namespace {
+
+// (Re)build the hierarchy from the pinned host copy of the scene table and enqueue
+// its copy to the device.  Device room is sized once for the most nodes the sphere
+// count can need (n - 1 interior nodes of a binary tree over n leaves at most).
+rt_status bvh_refresh(rt_scene* s, cudaStream_t st_) {
+    if (!s->host_current) return RT_ERR_UNSUPPORTED;
+    const float4* geo = reinterpret_cast<const float4*>(static_cast<const char*>(s->pinned) + sizeof(SceneHdr));
+    rtbvh::Result R;
+    rtbvh::build(geo, s->ns, &R);
+    if (!((double)R.r_scene < kBvhCoordLimit)) return RT_ERR_UNSUPPORTED;
+    const int n_nodes = (int)R.nodes.size();
+    const size_t bytes = bvh_bytes(n_nodes, s->ns);
+    cudaError_t e = cudaSuccess;
+    if (bytes > 0) {
+        if (!s->bvh_dev) {
+            const size_t cap = bvh_bytes(std::max(s->ns - 1, 1), s->ns);
+            e = cudaMalloc(&s->bvh_dev, cap);
+            if (e == cudaSuccess) e = cudaMallocHost(&s->bvh_pinned, cap);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->bvh_copy_done, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_status(e);
+            s->bvh_cap = cap;
+        } else {
+            e = cudaEventSynchronize(s->bvh_copy_done);  // the previous copy has left the staging buffer
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        if (bytes > s->bvh_cap) return RT_ERR_UNSUPPORTED;
+        unsigned char* h = static_cast<unsigned char*>(s->bvh_pinned);
+        std::memset(h, 0, bytes);
+        std::memcpy(h, R.nodes.data(), (size_t)n_nodes * sizeof(BvhNode));
+        std::memcpy(h + (size_t)n_nodes * sizeof(BvhNode), R.prim.data(), R.prim.size() * 4);
+        e = cudaMemcpyAsync(s->bvh_dev, h, bytes, cudaMemcpyHostToDevice, st_);
+        if (e == cudaSuccess) e = cudaEventRecord(s->bvh_copy_done, st_);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    s->bvh_info.n_nodes = n_nodes;
+    s->bvh_info.depth = R.depth;
+    s->bvh_info.max_leaf = R.max_leaf;
+    s->bvh_info.r_scene = R.r_scene;
+    s->bvh_state = 1;
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_scene_build_bvh(rt_scene* s, void* stream, rt_bvh_info* info) {
+    if (!s) return RT_ERR_INVALID_ARG;
+    const rt_status st = bvh_refresh(s, static_cast<cudaStream_t>(stream));
+    if (st == RT_OK && info) *info = s->bvh_info;
+    return st;
+}
+
+rt_status rt_bvh_build_host(const rt_scene_desc* desc, void* nodes, int32_t nodes_cap, int32_t* prim_idx,
+                            rt_bvh_info* info) {
+    rt_status st = validate_desc(desc);
+    if (st != RT_OK) return st;
+    std::vector<float4> geo((size_t)desc->n_spheres);
+    for (int i = 0; i < desc->n_spheres; ++i) {
+        const float* f = desc->spheres + 10 * (size_t)i;
+        geo[(size_t)i] = make_float4(f[0], f[1], f[2], (float)((double)f[3] * f[3]));
+    }
+    rtbvh::Result R;
+    rtbvh::build(geo.data(), desc->n_spheres, &R);
+    if (!((double)R.r_scene < kBvhCoordLimit)) return RT_ERR_UNSUPPORTED;
+    if (info) {
+        info->n_nodes = (int32_t)R.nodes.size();
+        info->depth = R.depth;
+        info->max_leaf = R.max_leaf;
+        info->r_scene = R.r_scene;
+    }
+    if (nodes) {
+        if (nodes_cap < (int32_t)R.nodes.size()) return RT_ERR_INVALID_ARG;
+        std::memcpy(nodes, R.nodes.data(), R.nodes.size() * sizeof(BvhNode));
+    }
+    if (prim_idx) std::memcpy(prim_idx, R.prim.data(), R.prim.size() * 4);
+    return RT_OK;
+}
+
 rt_status rt_scene_upload(const rt_scene_desc* desc, void* stream, rt_scene** out) {
     if (!out) return RT_ERR_INVALID_ARG;
     *out = nullptr;
@@ -510,6 +650,8 @@ rt_status rt_scene_update(rt_scene* s, const rt_scene_desc* desc, int32_t desc_o
         rt_pack_kernel<<<(n + 255) / 256, 256, 0, st_>>>(view_of(s), s->ns, desc->spheres, s->has_plane,
                                                          desc->plane, s->nl, desc->lights);
         g_launches++;
+        s->host_current = false;
+        if (s->bvh_state) s->bvh_state = 2;
         return cuda_status(cudaGetLastError());
     }
     rt_status st = validate_desc(desc);
@@ -519,7 +661,9 @@ rt_status rt_scene_update(rt_scene* s, const rt_scene_desc* desc, int32_t desc_o
     pack_host(desc, s->ns_pad, static_cast<unsigned char*>(s->pinned));
     e = cudaMemcpyAsync(s->dev, s->pinned, s->bytes, cudaMemcpyHostToDevice, st_);
     if (e == cudaSuccess) e = cudaEventRecord(s->copy_done, st_);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->host_current = true;
+    return s->bvh_state ? bvh_refresh(s, st_) : RT_OK;
 }
 
 rt_status rt_scene_free(rt_scene* s) {
@@ -528,6 +672,9 @@ rt_status rt_scene_free(rt_scene* s) {
     if (s->dev) cudaFree(s->dev);
     if (s->pinned) cudaFreeHost(s->pinned);
     if (s->copy_done) cudaEventDestroy(s->copy_done);
+    if (s->bvh_dev) cudaFree(s->bvh_dev);
+    if (s->bvh_pinned) cudaFreeHost(s->bvh_pinned);
+    if (s->bvh_copy_done) cudaEventDestroy(s->bvh_copy_done);
     delete s;
     return RT_OK;
 }
@@ -560,14 +707,41 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
     fr.rx1 = x0 + rw;
     fr.ry1 = y0 + rh;
     const int nwarps = (L.bx * L.by) / 32;
-    const bool chunked = use_tiled_loop(L, s->ns_pad);
-    const size_t smem = stage_smem_bytes(chunked, s->ns_pad, nwarps);
     const int hstage = L.staging == 2 ? 2 : 1;  // how the header (and the whole table) is staged
     const dim3 block(32, nwarps);
     const dim3 grid((rw + L.bx - 1) / L.bx, (rh + L.by - 1) / L.by);
     const size_t plane = (size_t)p->width * (size_t)p->height;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     float* hr = static_cast<float*>(hitrec_dev);
+    if (L.accel) {
+        if (s->bvh_state != 1) return RT_ERR_UNSUPPORTED;
+        for (int k = 0; k < 3; ++k)
+            if (!(std::fabs(cam->pos[k]) < kBvhCoordLimit)) return RT_ERR_UNSUPPORTED;
+        BvhView bv;
+        bv.nodes = static_cast<const BvhNode*>(s->bvh_dev);
+        bv.n_nodes = s->bvh_info.n_nodes;
+        bv.prim = reinterpret_cast<const int32_t*>(static_cast<const char*>(s->bvh_dev) +
+                                                   (size_t)bv.n_nodes * sizeof(BvhNode));
+        bv.r_scene = s->bvh_info.r_scene;
+        const size_t bb = bvh_bytes(bv.n_nodes, s->ns);
+        const size_t full = sizeof(SceneHdr) + (size_t)s->ns_pad * 16 + bb;
+        const bool staged = bv.n_nodes > 0 && full + 4096 <= (size_t)(max_smem_optin() - 1024);
+        const size_t smem = staged ? full : sizeof(SceneHdr);
+        const uint32_t stage_b = staged ? (uint32_t)bb : 0u;
+#define RT_BVH_LAUNCH(HR)                                                                                       \
+    do {                                                                                                        \
+        if ((st = ensure_smem(rt_fwd_bvh_kernel<HR>, smem)) != RT_OK) return st;                               \
+        rt_fwd_bvh_kernel<HR><<<grid, block, smem, st_>>>(view_of(s), bv, stage_b, fr, out_dev, out_pitch_bytes, \
+                                                         hr, plane, hstage, L.bx, L.by);                       \
+    } while (0)
+        if (hr) RT_BVH_LAUNCH(true);
+        else RT_BVH_LAUNCH(false);
+#undef RT_BVH_LAUNCH
+        g_launches++;
+        return cuda_status(cudaGetLastError());
+    }
+    const bool chunked = use_tiled_loop(L, s->ns_pad);
+    const size_t smem = stage_smem_bytes(chunked, s->ns_pad, nwarps);
 #define RT_FWD_LAUNCH(HR, CHK)                                                                                   \
     do {                                                                                                         \
         if ((st = ensure_smem(rt_fwd_kernel<HR, CHK>, smem)) != RT_OK) return st;                               \
@@ -728,6 +902,7 @@ rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_r
         return RT_ERR_INVALID_ARG;
     Launch L;
     if ((st = resolve_launch(cfg, &L)) != RT_OK) return st;
+    if (L.accel) return RT_ERR_UNSUPPORTED;
     const size_t need = rt_backward_workspace_bytes(s, p, cfg);
     if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 15) || workspace_bytes < need)
         return RT_ERR_INVALID_ARG;
@@ -813,6 +988,7 @@ rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera
                            size_t* smem_out, bool* chunked_out) {
     if (n < 1 || !scenes || !cams || !params || !outs || !pitches) return RT_ERR_INVALID_ARG;
     if (L.bx * L.by > kBatchMaxThreads) return RT_ERR_INVALID_ARG;
+    if (L.accel) return RT_ERR_UNSUPPORTED;
     if (n > RT_NOALLOC_MAX_FRAMES) return RT_ERR_EXCEEDS_SCRATCH;
     int order[RT_NOALLOC_MAX_FRAMES];
     int tiles[RT_NOALLOC_MAX_FRAMES];

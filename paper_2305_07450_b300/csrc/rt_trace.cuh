@@ -4,6 +4,7 @@
 // kernel, the batched persistent kernel and the adjoint's recompute mode.
 #pragma once
 
+#include "rt_bvh.cuh"
 #include "rt_device.cuh"
 
 namespace rtd {
@@ -21,6 +22,7 @@ struct StagedScene {
     float4* chunk;         // shared, this warp's kChunk entries (tiled loop)
     const float4* mat;     // global
     const float4* mat2;    // global
+    BvhView bvh;           // hierarchy over the spheres (ACC kernels only)
 };
 
 // Tiled loop: entries [c0, c0 + m) of the global table into the warp's slot, copied
@@ -87,12 +89,14 @@ __device__ __forceinline__ void closest_block(const float4* __restrict__ geo, in
     }
 }
 
-template <bool CH>
+template <bool CH, bool ACC = false>
 __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, float& t_out) {
     float tb = __int_as_float(0x7f800000);  // +inf
     int best = -1;
     const int n = sc.hdr->ns_pad;
-    if constexpr (CH) {
+    if constexpr (ACC) {
+        closest_bvh(sc.geo, sc.bvh, o, d, tb, best);
+    } else if constexpr (CH) {
         const unsigned mask = __activemask();
 #pragma unroll 1
         for (int c0 = 0; c0 < n; c0 += kChunk) {
@@ -156,12 +160,16 @@ __device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, u
     return __all_sync(mask, done);
 }
 
-template <int R, bool CH>
+template <int R, bool CH, bool ACC = false>
 __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, const f3 (&dir)[4],
                                                const float (&dist)[4], bool (&occ)[4]) {
     const int n = sc.hdr->ns_pad;
     const unsigned mask = __activemask();
-    if constexpr (CH) {
+    if constexpr (ACC) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (!occ[r]) occ[r] = occluded_bvh(sc.geo, sc.bvh, o, dir[r], dist[r]);
+    } else if constexpr (CH) {
         bool stop = false;
 #pragma unroll 1
         for (int c0 = 0; c0 < n && !stop; c0 += kChunk) {
@@ -253,7 +261,7 @@ __device__ __forceinline__ int rays_of_light(const Frame& fr, float4 Ls) {
     return (Ls.x > 0.0f || Ls.y > 0.0f) ? fr.nsamp : 1;
 }
 
-template <bool HITREC, bool CH>
+template <bool HITREC, bool CH, bool ACC = false>
 __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, f3 p,
                                               f3 p_lo, f3 n, f3 po, f3 d, float ks, float e, float* __restrict__ hr,
                                               size_t hr_k, size_t hr_plane) {
@@ -306,10 +314,10 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
             }
         }
         switch (R) {
-            case 1: occluded_group<1, CH>(sc, po, dir, dist, occ); break;
-            case 2: occluded_group<2, CH>(sc, po, dir, dist, occ); break;
-            case 3: occluded_group<3, CH>(sc, po, dir, dist, occ); break;
-            default: occluded_group<4, CH>(sc, po, dir, dist, occ); break;
+            case 1: occluded_group<1, CH, ACC>(sc, po, dir, dist, occ); break;
+            case 2: occluded_group<2, CH, ACC>(sc, po, dir, dist, occ); break;
+            case 3: occluded_group<3, CH, ACC>(sc, po, dir, dist, occ); break;
+            default: occluded_group<4, CH, ACC>(sc, po, dir, dist, occ); break;
         }
         // attribute the results to their lights in the same order
 #pragma unroll
@@ -408,7 +416,7 @@ __device__ __forceinline__ f3 offset_origin(const HitGeom& hg, float eps, f3& lo
 // reflection recursion of Section 3.7.1 is unrolled forward with a scalar
 // throughput: k < D adds T((1 - rho) A c + S) and sets T *= rho A; k = D adds
 // T(A c + S); a miss ends the path.  HITREC: write (id, t, vis_l) per bounce.
-template <bool HITREC, bool CH>
+template <bool HITREC, bool CH, bool ACC = false>
 __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame& fr, int x, int y,
                                               float* __restrict__ hr, size_t hr_plane, size_t hr_pix) {
     const SceneHdr& h = *sc.hdr;
@@ -421,7 +429,7 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
 #pragma unroll 1
     for (; k <= fr.D; ++k) {
         float t;
-        const int id = closest_hit<CH>(sc, o, d, t);
+        const int id = closest_hit<CH, ACC>(sc, o, d, t);
         if (HITREC) {
             float* rec = hr + (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
             rec[0] = __int_as_float(id);
@@ -433,7 +441,7 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
         const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);
         const float4 m = hg.m, m2 = hg.m2;
         const size_t hr_k = (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
-        const HitShade sh = shade_hit<HITREC, CH>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+        const HitShade sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
         const float A = sh.A, S = sh.S;
         if (k < fr.D) {
             const float w = T * (1.0f - m2.y) * A;
@@ -474,13 +482,13 @@ __device__ __forceinline__ uint32_t pack_rgba8(float3 c) {
 // 32 lanes of the warp must call (the RGBA8 path gathers four horizontally adjacent
 // pixels, lanes 4j..4j+3, into one 16-byte store; rx0 is a multiple of 8); `valid`
 // marks lanes whose pixel is inside the rendered region.
-template <bool HITREC, bool CH>
+template <bool HITREC, bool CH, bool ACC = false>
 __device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
                                              void* __restrict__ out, size_t pitch, float* __restrict__ hr,
                                              size_t hr_plane) {
     const int lane = threadIdx.x & 31;
     float3 c = make_float3(0.f, 0.f, 0.f);
-    if (valid) c = trace_pixel<HITREC, CH>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
+    if (valid) c = trace_pixel<HITREC, CH, ACC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
     const int lx = x - fr.rx0, ly = y - fr.ry0;
     if (fr.fmt == RT_OUT_F32) {
         if (valid)

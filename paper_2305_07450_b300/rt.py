@@ -45,7 +45,15 @@ class RenderParams(C.Structure):
 
 class LaunchConfig(C.Structure):
     _fields_ = [("block_x", C.c_int32), ("block_y", C.c_int32), ("staging", C.c_int32),
-                ("min_blocks_per_sm", C.c_int32)]
+                ("min_blocks_per_sm", C.c_int32), ("accel", C.c_int32)]
+
+
+class BvhInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("depth", C.c_int32), ("max_leaf", C.c_int32), ("r_scene", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {"n_nodes": int(self.n_nodes), "depth": int(self.depth), "max_leaf": int(self.max_leaf),
+                "r_scene": float(self.r_scene)}
 
 
 _lib = None
@@ -99,6 +107,10 @@ def lib():
                                               C.POINTER(sz), C.POINTER(LaunchConfig), vp]
         L.rt_render_batch_noalloc.restype = C.c_int
         L.rt_batch_free.argtypes = [vp]
+        L.rt_scene_build_bvh.argtypes = [vp, vp, C.POINTER(BvhInfo)]
+        L.rt_scene_build_bvh.restype = C.c_int
+        L.rt_bvh_build_host.argtypes = [C.POINTER(SceneDesc), vp, i32, vp, C.POINTER(BvhInfo)]
+        L.rt_bvh_build_host.restype = C.c_int
         for name in ("rt_scene_upload", "rt_scene_update", "rt_scene_free", "rt_render",
                      "rt_device_errors", "rt_render_batch", "rt_batch_create", "rt_batch_launch",
                      "rt_batch_free"):
@@ -189,6 +201,13 @@ class DeviceScene:
                 assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
         check("rt_scene_update", lib().rt_scene_update(self._h, C.byref(d), 1, _stream(stream)))
 
+    def build_bvh(self, stream=None) -> dict:
+        """rt_scene_build_bvh: (re)build the sphere hierarchy that launch
+        {"accel": 1} renders through; returns its figures."""
+        info = BvhInfo()
+        check("rt_scene_build_bvh", lib().rt_scene_build_bvh(self._h, _stream(stream), C.byref(info)))
+        return info.as_dict()
+
     @property
     def nbytes(self) -> int:
         """Bytes of the device scene table (one host-to-device upload)."""
@@ -208,6 +227,23 @@ class DeviceScene:
             self.close()
         except Exception:
             pass
+
+
+NODE_DTYPE = np.dtype([("a_lo", "<f4", 3), ("a_hi", "<f4", 3), ("b_lo", "<f4", 3), ("b_hi", "<f4", 3),
+                       ("ref", "<i4", 2), ("zero", "<i4", 2)])
+
+
+def bvh_build_host(scene: scenes.Scene):
+    """rt_bvh_build_host: the hierarchy the device would use, built on the host only
+    (no GPU needed).  Returns (nodes as a NODE_DTYPE array, prim_idx, info dict)."""
+    d, *keep = DeviceScene._desc(scene)
+    info = BvhInfo()
+    check("rt_bvh_build_host", lib().rt_bvh_build_host(C.byref(d), None, 0, None, C.byref(info)))
+    nodes = np.zeros(max(int(info.n_nodes), 1), NODE_DTYPE)
+    prim = np.zeros(max(scene.n_spheres, 1), np.int32)
+    check("rt_bvh_build_host", lib().rt_bvh_build_host(C.byref(d), nodes.ctypes.data, int(info.n_nodes),
+                                                       prim.ctypes.data, C.byref(info)))
+    return nodes[: int(info.n_nodes)], prim[: scene.n_spheres], info.as_dict()
 
 
 def alloc_output(params: scenes.Params, device="cuda") -> tuple[torch.Tensor, int]:
