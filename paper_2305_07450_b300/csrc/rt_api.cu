@@ -150,7 +150,7 @@ __global__ void rt_pack_kernel(SceneView sv, int ns, const float* __restrict__ s
     float4* mat2 = const_cast<float4*>(sv.mat2);
     if (i < ns) {
         const float* f = sph + 10 * (size_t)i;
-        geo[i] = make_float4(f[0], f[1], f[2], f[3] * f[3]);
+        sphere_put(geo, i, make_float4(f[0], f[1], f[2], -(f[3] * f[3])));
         mat[i] = make_float4(f[4], f[5], f[6], f[7]);
         mat2[i] = make_float4(f[8], f[9], f[3], __frcp_rn(f[3]));
     } else if (i == ns) {
@@ -248,11 +248,11 @@ void pack_host(const rt_scene_desc* d, int ns_pad, unsigned char* blob) {
     for (int i = 0; i < ns_pad; ++i) {
         if (i < d->n_spheres) {
             const float* f = d->spheres + 10 * (size_t)i;
-            geo[i] = make_float4(f[0], f[1], f[2], (float)((double)f[3] * f[3]));
+            sphere_put(geo, i, make_float4(f[0], f[1], f[2], -(float)((double)f[3] * f[3])));
             mat[i] = make_float4(f[4], f[5], f[6], f[7]);
             mat2[i] = make_float4(f[8], f[9], f[3], (float)(1.0 / (double)f[3]));
         } else {
-            geo[i] = make_float4(0.f, 0.f, 0.f, -1.f);  // never hit, never blocks
+            sphere_put(geo, i, make_float4(0.f, 0.f, 0.f, 1.f));  // never hit, never blocks
             mat[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             mat2[i] = make_float4(0.f, 0.f, 1.f, 1.f);
         }
@@ -580,10 +580,10 @@ rt_status rt_bvh_build_host(const rt_scene_desc* desc, void* nodes, int32_t node
                             rt_bvh_info* info) {
     rt_status st = validate_desc(desc);
     if (st != RT_OK) return st;
-    std::vector<float4> geo((size_t)desc->n_spheres);
+    std::vector<float4> geo((size_t)pad_spheres(desc->n_spheres));  // the paired table, as packed for the device
     for (int i = 0; i < desc->n_spheres; ++i) {
         const float* f = desc->spheres + 10 * (size_t)i;
-        geo[(size_t)i] = make_float4(f[0], f[1], f[2], (float)((double)f[3] * f[3]));
+        sphere_put(geo.data(), i, make_float4(f[0], f[1], f[2], -(float)((double)f[3] * f[3])));
     }
     rtbvh::Result R;
     rtbvh::build(geo.data(), desc->n_spheres, &R);

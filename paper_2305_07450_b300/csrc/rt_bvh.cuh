@@ -48,26 +48,26 @@ __host__ __device__ inline size_t bvh_bytes(int n_nodes, int ns) {
 }
 
 // ---------------------------------------------------------------- per sphere
-// The brute-force block tests of Sections 3.4.1 and 3.6 for one sphere, the same
-// operations in the same order (closest root; blocked segment).
+// The brute-force block tests of Sections 3.4.1 and 3.6 for one sphere g = (c, -r^2),
+// element for element the operations of the packed pair tests, in the same order
+// (closest root; blocked segment o + u V, u = clamp(oc.W, 0, 1), -V = nv).
 __device__ __forceinline__ bool sphere_root_t(float4 g, f3 o, f3 d, float& t) {
-    const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
+    const float ocx = g.x + (-o.x), ocy = g.y + (-o.y), ocz = g.z + (-o.z);
     const float tca = fmaf(ocx, d.x, fmaf(ocy, d.y, ocz * d.z));
-    const float lx = fmaf(-tca, d.x, ocx), ly = fmaf(-tca, d.y, ocy), lz = fmaf(-tca, d.z, ocz);
-    const float disc = fmaf(-lx, lx, fmaf(-ly, ly, fmaf(-lz, lz, g.w)));
-    if (!(disc >= 0.0f)) return false;
-    const float s = __fsqrt_rn(disc);
+    const float lx = fmaf(tca, -d.x, ocx), ly = fmaf(tca, -d.y, ocy), lz = fmaf(tca, -d.z, ocz);
+    const float m = fmaf(lx, lx, fmaf(ly, ly, fmaf(lz, lz, g.w)));
+    if (!(m < 0.0f)) return false;
+    const float s = __fsqrt_rn(-m);
     t = tca - s;
     if (t <= 0.0f) t = tca + s;
     return t > 0.0f;
 }
 
-__device__ __forceinline__ bool segment_blocked(float4 g, f3 o, f3 dir, float dist) {
-    const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
-    const float tca = fmaf(ocx, dir.x, fmaf(ocy, dir.y, ocz * dir.z));
-    const float tc = fminf(fmaxf(tca, 0.0f), dist);
-    const float qx = fmaf(-tc, dir.x, ocx), qy = fmaf(-tc, dir.y, ocy), qz = fmaf(-tc, dir.z, ocz);
-    const float e = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, -g.w)));
+__device__ __forceinline__ bool segment_blocked(float4 g, f3 o, f3 w, f3 nv) {
+    const float ocx = g.x + (-o.x), ocy = g.y + (-o.y), ocz = g.z + (-o.z);
+    const float u = fma_sat(ocx, w.x, fmaf(ocy, w.y, ocz * w.z));
+    const float qx = fmaf(u, nv.x, ocx), qy = fmaf(u, nv.y, ocy), qz = fmaf(u, nv.z, ocz);
+    const float e = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, g.w)));
     return e < 0.0f;
 }
 
@@ -169,7 +169,7 @@ __device__ __forceinline__ void closest_bvh(const float4* __restrict__ geo, cons
             for (int k = 0; k < cnt; ++k) {
                 const int i = bv.prim[first + k];
                 float t;
-                if (sphere_root_t(geo[i], o, d, t) && (t < tb || (t == tb && i < best))) {
+                if (sphere_root_t(sphere_at(geo, i), o, d, t) && (t < tb || (t == tb && i < best))) {
                     tb = t;
                     best = i;
                 }
@@ -190,11 +190,11 @@ __device__ __forceinline__ void closest_bvh(const float4* __restrict__ geo, cons
     }
 }
 
-// Any sphere blocking the segment o + s dir, s in [0, dist]: the OR of the
-// brute-force predicate over the spheres of the entered leaves; the first blocker
-// ends the walk.
+// Any sphere blocking the segment o + s dir, s in [0, dist] (o + u V, u in [0, 1],
+// for the sphere test): the OR of the brute-force predicate over the spheres of the
+// entered leaves; the first blocker ends the walk.
 __device__ __forceinline__ bool occluded_bvh(const float4* __restrict__ geo, const BvhView& bv, f3 o, f3 dir,
-                                             float dist) {
+                                             float dist, f3 w, f3 nv) {
     if (bv.n_nodes <= 0) return false;
     const RayInv q = ray_inv(o, dir, bv.r_scene);
     int stack[kBvhStack];
@@ -227,7 +227,7 @@ __device__ __forceinline__ bool occluded_bvh(const float4* __restrict__ geo, con
             const int first = v >> 4, cnt = (v & 15) + 1;
 #pragma unroll 1
             for (int k = 0; k < cnt; ++k)
-                if (segment_blocked(geo[bv.prim[first + k]], o, dir, dist)) return true;
+                if (segment_blocked(sphere_at(geo, bv.prim[first + k]), o, w, nv)) return true;
         }
         if (sp == 0) break;
         ref = stack[--sp];

@@ -210,7 +210,7 @@ class Builder {
     }
 };
 
-// geo[i] = (cx, cy, cz, r^2) as the kernels hold it.
+// geo: the paired sphere table as the kernels hold it (sphere_at gives (cx, cy, cz, -r^2)).
 inline void build(const float4* geo, int ns, Result* out) {
     out->nodes.clear();
     out->prim.clear();
@@ -221,8 +221,8 @@ inline void build(const float4* geo, int ns, Result* out) {
     std::vector<Prim> P((size_t)ns);
     double rs = 0.0;
     for (int i = 0; i < ns; ++i) {
-        const float4 g = geo[i];
-        const double r = std::sqrt((double)g.w);
+        const float4 g = rtd::sphere_at(geo, i);
+        const double r = std::sqrt(-(double)g.w);
         Prim& p = P[(size_t)i];
         p.c[0] = g.x;
         p.c[1] = g.y;

@@ -33,6 +33,21 @@ __device__ __forceinline__ f3 normalize_rn(f3 a, float* len_out = nullptr) {
     return scl(a, inv);
 }
 
+// Packed FP32 pairs (sm_100 family): one instruction performs two FP32 operations,
+// each rounded exactly as its scalar counterpart, so a pair of sphere tests costs
+// one issue slot per step instead of two.
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a * b + c rounded once, then clamped to [0, 1] (NaN to 0): the parameter of the
+// point of a segment closest to a centre.
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+    float d;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Error-free sum (Knuth's TwoSum): s + err == a + b exactly.  Used only per hit, to
 // carry ray origins as unevaluated hi + lo pairs: positions of tens of units lose
 // ~1e-6 to FP32 rounding, which a small sphere turns into ~1e-6 rad of normal.
@@ -65,7 +80,9 @@ struct __align__(16) SceneHdr {
 };
 static_assert(sizeof(SceneHdr) % 16 == 0, "header must keep 16-byte alignment");
 
-// geo[i]  = (cx, cy, cz, r^2)   -- pad entries (0, 0, 0, -1): disc < 0, never hit
+// geo: spheres in pairs (2q, 2q + 1), two float4 per pair, so that one packed
+// instruction tests both:  geo[2q] = (cx0, cx1, cy0, cy1), geo[2q + 1] = (cz0, cz1,
+// -r0^2, -r1^2).  Pad entries: centre 0, -r^2 = +1 (never hit, never block).
 // mat[i]  = (albedo r, g, b, k_s)
 // mat2[i] = (spec_exp, reflectivity, r, 1/r)
 struct SceneView {
@@ -76,6 +93,28 @@ struct SceneView {
 };
 
 __host__ __device__ inline size_t scene_geo_offset() { return sizeof(SceneHdr); }
+
+// Sphere i of the paired geometry table as (cx, cy, cz, -r^2).
+__host__ __device__ inline float4 sphere_at(const float4* geo, int i) {
+    const float4 a = geo[i & ~1], b = geo[(i & ~1) + 1];
+    return (i & 1) ? make_float4(a.y, a.w, b.y, b.w) : make_float4(a.x, a.z, b.x, b.z);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ float4 sphere_ldg(const float4* geo, int i) {
+    const float4 a = __ldg(geo + (i & ~1)), b = __ldg(geo + (i & ~1) + 1);
+    return (i & 1) ? make_float4(a.y, a.w, b.y, b.w) : make_float4(a.x, a.z, b.x, b.z);
+}
+#endif
+// Write sphere i (cx, cy, cz, -r^2) into the paired table.
+__host__ __device__ inline void sphere_put(float4* geo, int i, float4 s) {
+    float4& a = geo[i & ~1];
+    float4& b = geo[(i & ~1) + 1];
+    if (i & 1) {
+        a.y = s.x; a.w = s.y; b.y = s.z; b.w = s.w;
+    } else {
+        a.x = s.x; a.z = s.y; b.x = s.z; b.z = s.w;
+    }
+}
 __host__ __device__ inline size_t scene_bytes(int ns_pad) { return sizeof(SceneHdr) + (size_t)ns_pad * 48; }
 __host__ __device__ inline int pad_spheres(int ns) { return (ns + kPad - 1) / kPad * kPad; }
 

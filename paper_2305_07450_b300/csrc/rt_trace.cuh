@@ -54,35 +54,51 @@ __device__ __forceinline__ f3 primary_dir(const Frame& fr, int x, int y) {
 // Closest of all primitives by brute force; spheres 0..N-1 then the plane N; a
 // strictly smaller distance wins, so ties keep the lower index.  Sphere test in the
 // well-conditioned form: with oc = c - o and tca = oc.d, the squared distance of
-// the centre from the ray's line is |oc - tca d|^2, so disc = r^2 - |oc - tca d|^2
-// avoids the cancellation of tca^2 - |oc|^2 for distant spheres.  Roots tca -+
-// sqrt(disc); the near one if it is > 0, else the far one.  Spheres are taken in
-// blocks of kPad: the discriminants of a block are computed branch-free, and the
-// roots only when one of them is non-negative (one branch per block).
-// One block of kPad spheres (at geo[0..kPad)) for the closest hit; base = index of geo[0].
-__device__ __forceinline__ void closest_block(const float4* __restrict__ geo, int base, f3 o, f3 d, float& tb,
+// the centre from the ray's line is |oc - tca d|^2, so m = |oc - tca d|^2 - r^2
+// (the negated discriminant) avoids the cancellation of tca^2 - |oc|^2 for distant
+// spheres; a hit needs m < 0, at tca -+ sqrt(-m): the near root if it is > 0, else
+// the far one.  The two spheres of a pair are tested by the same packed
+// instructions; a block of kPad spheres computes its m branch-free and takes the
+// roots only when one of them is negative (one branch per block).
+struct RayPair {  // -o, d and -d in both halves of a pair
+    float2 nox, noy, noz, dx, dy, dz, ndx, ndy, ndz;
+};
+__device__ __forceinline__ RayPair ray_pair(f3 o, f3 d) {
+    return RayPair{dup2(-o.x), dup2(-o.y), dup2(-o.z), dup2(d.x), dup2(d.y),
+                   dup2(d.z),  dup2(-d.x), dup2(-d.y), dup2(-d.z)};
+}
+
+// One block of kPad spheres (kPad / 2 pairs at geo[0..kPad)); base = index of its first sphere.
+__device__ __forceinline__ void closest_block(const float4* __restrict__ geo, int base, const RayPair& r, float& tb,
                                               int& best) {
-    float disc[kPad], tca[kPad];
-    float dmax = -1.0f;
+    float2 tca[kPad / 2], m[kPad / 2];
+    uint32_t neg = 0;
 #pragma unroll
-    for (int j = 0; j < kPad; ++j) {
-        const float4 g = geo[j];
-        const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
-        tca[j] = fmaf(ocx, d.x, fmaf(ocy, d.y, ocz * d.z));
-        const float lx = fmaf(-tca[j], d.x, ocx), ly = fmaf(-tca[j], d.y, ocy), lz = fmaf(-tca[j], d.z, ocz);
-        disc[j] = fmaf(-lx, lx, fmaf(-ly, ly, fmaf(-lz, lz, g.w)));
-        dmax = fmaxf(dmax, disc[j]);
+    for (int q = 0; q < kPad / 2; ++q) {
+        const float4 A = geo[2 * q], B = geo[2 * q + 1];
+        const float2 ocx = add2(make_float2(A.x, A.y), r.nox);
+        const float2 ocy = add2(make_float2(A.z, A.w), r.noy);
+        const float2 ocz = add2(make_float2(B.x, B.y), r.noz);
+        tca[q] = fma2(ocx, r.dx, fma2(ocy, r.dy, mul2(ocz, r.dz)));
+        const float2 lx = fma2(tca[q], r.ndx, ocx), ly = fma2(tca[q], r.ndy, ocy), lz = fma2(tca[q], r.ndz, ocz);
+        m[q] = fma2(lx, lx, fma2(ly, ly, fma2(lz, lz, make_float2(B.z, B.w))));
+        neg |= __float_as_uint(m[q].x) | __float_as_uint(m[q].y);
     }
-    if (dmax >= 0.0f) {
+    if (neg >> 31) {
 #pragma unroll
-        for (int j = 0; j < kPad; ++j) {
-            if (disc[j] >= 0.0f) {
-                const float s = __fsqrt_rn(disc[j]);
-                float t = tca[j] - s;
-                if (t <= 0.0f) t = tca[j] + s;
-                if (t > 0.0f && t < tb) {
-                    tb = t;
-                    best = base + j;
+        for (int q = 0; q < kPad / 2; ++q) {
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const float mm = hf ? m[q].y : m[q].x;
+                if (mm < 0.0f) {
+                    const float tc = hf ? tca[q].y : tca[q].x;
+                    const float s = __fsqrt_rn(-mm);
+                    float t = tc - s;
+                    if (t <= 0.0f) t = tc + s;
+                    if (t > 0.0f && t < tb) {
+                        tb = t;
+                        best = base + 2 * q + hf;
+                    }
                 }
             }
         }
@@ -96,18 +112,21 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
     const int n = sc.hdr->ns_pad;
     if constexpr (ACC) {
         closest_bvh(sc.geo, sc.bvh, o, d, tb, best);
-    } else if constexpr (CH) {
-        const unsigned mask = __activemask();
-#pragma unroll 1
-        for (int c0 = 0; c0 < n; c0 += kChunk) {
-            const int m = min(kChunk, n - c0);
-            stage_chunk(sc, mask, c0, m);
-#pragma unroll 1
-            for (int i0 = 0; i0 < m; i0 += kPad) closest_block(sc.chunk + i0, c0 + i0, o, d, tb, best);
-        }
     } else {
+        const RayPair rp = ray_pair(o, d);
+        if constexpr (CH) {
+            const unsigned mask = __activemask();
 #pragma unroll 1
-        for (int i0 = 0; i0 < n; i0 += kPad) closest_block(sc.geo + i0, i0, o, d, tb, best);
+            for (int c0 = 0; c0 < n; c0 += kChunk) {
+                const int m = min(kChunk, n - c0);
+                stage_chunk(sc, mask, c0, m);
+#pragma unroll 1
+                for (int i0 = 0; i0 < m; i0 += kPad) closest_block(sc.chunk + i0, c0 + i0, rp, tb, best);
+            }
+        } else {
+#pragma unroll 1
+            for (int i0 = 0; i0 < n; i0 += kPad) closest_block(sc.geo + i0, i0, rp, tb, best);
+        }
     }
     const SceneHdr& h = *sc.hdr;
     if (h.has_plane) {
@@ -126,67 +145,96 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
 }
 
 // ---------------------------------------------------------------- Section 3.6
-// Any-hit of R shadow segments that leave the same origin o (one shading point):
-// segment r runs along unit dir[r] for length dist[r].  For a sphere a segment is
-// blocked iff its closest point to the centre is inside the ball:
-// tc = clamp(oc.dir, 0, dist), |oc - tc dir|^2 < r^2.  With every light outside
-// every sphere (checked at upload) this is the same predicate as "a root of the
-// ray-sphere quadratic lies in (0, dist)".  oc = c - o and the shared-memory load
-// of the sphere are shared by the R segments.  occ[r] enters true for unused
-// slots.  The loop runs in blocks of kPad spheres and leaves once every segment of
-// every active lane is blocked: the method's early break (Section 3.6 cast-shadows
-// listing), taken warp-wide.
-// One block of kPad spheres (at geo[0..kPad)) against R segments; returns true
-// when every segment of every lane in `mask` is blocked.
+// Any-hit of R shadow segments that leave the same origin o (one shading point).
+// Segment r is o + u V_r, u in [0, 1], V_r = dist_r dir_r; it is blocked by a sphere
+// iff its point closest to the centre lies inside the ball: u* = clamp(oc.W_r, 0,
+// 1) with W_r = dir_r / dist_r (the clamp is the saturation of the last FMA), and
+// |oc - u* V_r|^2 - r^2 < 0.  That is the paper's "a root in (0, dist)" whenever
+// the light is outside the sphere (checked at upload), including origins inside a
+// sphere.  The sign bits of the pair's two results are OR-ed into a per-segment
+// word; oc = c - o and the sphere loads are shared by the R segments.  The loop
+// runs in blocks of kPad spheres and leaves once every segment of every active lane
+// is blocked: the method's early break (Section 3.6 cast-shadows listing), taken
+// warp-wide.
+// Shadow segments traced together from one shading point (shared sphere loads).
+constexpr int kShadowGroup = 4;
+
+struct SegPair {  // segment r: W in both halves (x also scalar), -V in both halves
+    float wx;
+    float2 wy, wz, nvx, nvy, nvz;
+};
+__device__ __forceinline__ SegPair seg_pair(f3 w, f3 nv) {
+    return SegPair{w.x, dup2(w.y), dup2(w.z), dup2(nv.x), dup2(nv.y), dup2(nv.z)};
+}
+
+// One block of kPad spheres (kPad / 2 pairs at geo[0..kPad)) against R segments;
+// returns true when every segment of every lane in `mask` is blocked.
 template <int R>
-__device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, unsigned mask, f3 o,
-                                               const f3 (&dir)[4], const float (&dist)[4], bool (&occ)[4]) {
+__device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, unsigned mask, const RayPair& o2,
+                                               const SegPair (&sg)[kShadowGroup], uint32_t (&acc)[kShadowGroup]) {
 #pragma unroll
-    for (int j = 0; j < kPad; ++j) {
-        const float4 g = geo[j];
-        const float ocx = g.x - o.x, ocy = g.y - o.y, ocz = g.z - o.z;
+    for (int q = 0; q < kPad / 2; ++q) {
+        const float4 A = geo[2 * q], B = geo[2 * q + 1];
+        const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
+        const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
+        const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
+        const float2 nr = make_float2(B.z, B.w);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float tca = fmaf(ocx, dir[r].x, fmaf(ocy, dir[r].y, ocz * dir[r].z));
-            const float tc = fminf(fmaxf(tca, 0.0f), dist[r]);
-            const float qx = fmaf(-tc, dir[r].x, ocx), qy = fmaf(-tc, dir[r].y, ocy), qz = fmaf(-tc, dir[r].z, ocz);
-            const float e = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, -g.w)));
-            occ[r] = occ[r] || (e < 0.0f);
+            const float2 t = fma2(ocy, sg[r].wy, mul2(ocz, sg[r].wz));
+            const float2 u = make_float2(fma_sat(ocx.x, sg[r].wx, t.x), fma_sat(ocx.y, sg[r].wx, t.y));
+            const float2 qx = fma2(u, sg[r].nvx, ocx), qy = fma2(u, sg[r].nvy, ocy), qz = fma2(u, sg[r].nvz, ocz);
+            const float2 e = fma2(qx, qx, fma2(qy, qy, fma2(qz, qz, nr)));
+            acc[r] |= __float_as_uint(e.x) | __float_as_uint(e.y);
         }
     }
     bool done = true;
 #pragma unroll
-    for (int r = 0; r < R; ++r) done = done && occ[r];
+    for (int r = 0; r < R; ++r) done = done && (acc[r] >> 31);
     return __all_sync(mask, done);
 }
 
+// occ[r] enters true for unused slots (and leaves true for blocked segments).
 template <int R, bool CH, bool ACC = false>
-__device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, const f3 (&dir)[4],
-                                               const float (&dist)[4], bool (&occ)[4]) {
+__device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, const f3 (&dir)[kShadowGroup],
+                                               const float (&dist)[kShadowGroup], const f3 (&w)[kShadowGroup], const f3 (&nv)[kShadowGroup],
+                                               bool (&occ)[kShadowGroup]) {
     const int n = sc.hdr->ns_pad;
-    const unsigned mask = __activemask();
     if constexpr (ACC) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (!occ[r]) occ[r] = occluded_bvh(sc.geo, sc.bvh, o, dir[r], dist[r]);
-    } else if constexpr (CH) {
-        bool stop = false;
+            if (!occ[r]) occ[r] = occluded_bvh(sc.geo, sc.bvh, o, dir[r], dist[r], w[r], nv[r]);
+    } else {
+        const unsigned mask = __activemask();
+        const RayPair o2 = ray_pair(o, mk3(0.f, 0.f, 0.f));
+        SegPair sg[kShadowGroup];
+        uint32_t acc[kShadowGroup];
+#pragma unroll
+        for (int r = 0; r < kShadowGroup; ++r) {
+            sg[r] = seg_pair(w[r], nv[r]);
+            acc[r] = occ[r] ? 0x80000000u : 0u;
+        }
+        if constexpr (CH) {
+            bool stop = false;
 #pragma unroll 1
-        for (int c0 = 0; c0 < n && !stop; c0 += kChunk) {
-            const int m = min(kChunk, n - c0);
-            stage_chunk(sc, mask, c0, m);
+            for (int c0 = 0; c0 < n && !stop; c0 += kChunk) {
+                const int m = min(kChunk, n - c0);
+                stage_chunk(sc, mask, c0, m);
 #pragma unroll 1
-            for (int i0 = 0; i0 < m; i0 += kPad) {
-                if (occluded_block<R>(sc.chunk + i0, mask, o, dir, dist, occ)) {
-                    stop = true;
-                    break;
+                for (int i0 = 0; i0 < m; i0 += kPad) {
+                    if (occluded_block<R>(sc.chunk + i0, mask, o2, sg, acc)) {
+                        stop = true;
+                        break;
+                    }
                 }
             }
-        }
-    } else {
+        } else {
 #pragma unroll 1
-        for (int i0 = 0; i0 < n; i0 += kPad)
-            if (occluded_block<R>(sc.geo + i0, mask, o, dir, dist, occ)) break;
+            for (int i0 = 0; i0 < n; i0 += kPad)
+                if (occluded_block<R>(sc.geo + i0, mask, o2, sg, acc)) break;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) occ[r] = (acc[r] >> 31) != 0;
     }
     const SceneHdr& h = *sc.hdr;
     if (h.has_plane) {
@@ -286,16 +334,18 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
     const unsigned mask = __activemask();
 #pragma unroll 1
     while (true) {
-        const int kr = min(4, total - done);
+        const int kr = min(kShadowGroup, total - done);
         const int R = (int)__reduce_max_sync(mask, (unsigned)kr);
         if (R == 0) break;
-        f3 dir[4];
-        float dist[4];
-        bool occ[4];
+        f3 dir[kShadowGroup], sw[kShadowGroup], snv[kShadowGroup];  // direction, W and -V of each segment
+        float dist[kShadowGroup];
+        bool occ[kShadowGroup];
         int l = cl, s = cs;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kShadowGroup; ++j) {
             dir[j] = mk3(0.f, 1.f, 0.f);
+            sw[j] = mk3(0.f, 0.f, 0.f);
+            snv[j] = mk3(0.f, 0.f, 0.f);
             dist[j] = 0.0f;
             occ[j] = true;
             if (j < kr) {
@@ -305,6 +355,8 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
                 const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
                                                                    : xyz(Lp);
                 dir[j] = normalize_rn(sub(sub(X, p), p_lo), &dist[j]);
+                sw[j] = scl(dir[j], __frcp_rn(dist[j]));
+                snv[j] = scl(dir[j], -dist[j]);
                 occ[j] = false;
                 if (++s == nr) {
                     s = 0;
@@ -313,15 +365,18 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
                 }
             }
         }
-        switch (R) {
-            case 1: occluded_group<1, CH, ACC>(sc, po, dir, dist, occ); break;
-            case 2: occluded_group<2, CH, ACC>(sc, po, dir, dist, occ); break;
-            case 3: occluded_group<3, CH, ACC>(sc, po, dir, dist, occ); break;
-            default: occluded_group<4, CH, ACC>(sc, po, dir, dist, occ); break;
+        if (kShadowGroup <= 1 || R == 1) {
+            occluded_group<1, CH, ACC>(sc, po, dir, dist, sw, snv, occ);
+        } else if (kShadowGroup == 2 || R == 2) {
+            occluded_group<(kShadowGroup < 2 ? 1 : 2), CH, ACC>(sc, po, dir, dist, sw, snv, occ);
+        } else if (kShadowGroup == 3 || R == 3) {
+            occluded_group<(kShadowGroup < 3 ? 1 : 3), CH, ACC>(sc, po, dir, dist, sw, snv, occ);
+        } else {
+            occluded_group<(kShadowGroup < 4 ? 1 : 4), CH, ACC>(sc, po, dir, dist, sw, snv, occ);
         }
         // attribute the results to their lights in the same order
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kShadowGroup; ++j) {
             if (j < kr) {
                 cnt += occ[j] ? 0 : 1;
                 const float4 Lp = h.light_p[cl];
@@ -367,7 +422,7 @@ __device__ __forceinline__ HitGeom hit_geometry(const StagedScene& sc, int id, f
     const SceneHdr& h = *sc.hdr;
     HitGeom hg;
     if (id < h.ns) {
-        const float4 g = CH ? __ldg(sc.geo_g + id) : sc.geo[id];
+        const float4 g = CH ? sphere_ldg(sc.geo_g, id) : sphere_at(sc.geo, id);  // (c, -r^2)
         hg.m = __ldg(sc.mat + id);
         hg.m2 = __ldg(sc.mat2 + id);
         f3 e;
@@ -376,7 +431,7 @@ __device__ __forceinline__ HitGeom hit_geometry(const StagedScene& sc, int id, f
         const float tca = dot(och, d) + dot(ocl, d);
         f3 l = add(fma3(d, -tca, och), ocl);
         l = fma3(d, -dot(l, d), l);
-        const float disc = fmaf(-l.x, l.x, fmaf(-l.y, l.y, fmaf(-l.z, l.z, g.w)));
+        const float disc = fmaf(-l.x, l.x, fmaf(-l.y, l.y, fmaf(-l.z, l.z, -g.w)));
         const float sq = __fsqrt_rn(fmaxf(disc, 0.0f));
         const float sgn = (tca - sq > 0.0f) ? -sq : sq;  // near root, else far root
         const f3 pc = mk3(fmaf(sgn, d.x, -l.x), fmaf(sgn, d.y, -l.y), fmaf(sgn, d.z, -l.z));
