@@ -500,6 +500,24 @@ def run_reference(args):
     }
 
 
+def profile_render(args):
+    """Only rt_render of the workload, warmup + steps times, with the library's default
+    launch (16x8 pixels, TMA staging): the program ncu captures for the forward kernel."""
+    import torch
+    from paper_2305_07450_b300 import rt
+    w = workload(args.workload)
+    ds = rt.DeviceScene(w.scene)
+    out, pitch = rt.alloc_output(w.params)
+    launch = {"accel": 1} if args.accel else None
+    if args.accel:
+        ds.build_bvh()
+    for _ in range(args.warmup + args.steps):
+        rt.render(ds, w.camera, w.params, out=out, pitch=pitch, launch=launch)
+    torch.cuda.synchronize()
+    assert rt.device_errors() == 0
+    print(json.dumps({"profile_render": w.name, "accel": bool(args.accel), "launches": args.warmup + args.steps}))
+
+
 def profile_batch(args):
     import torch
     from paper_2305_07450_b300 import rt
@@ -524,6 +542,9 @@ def main(argv=None):
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the 720p/1080p/batch measurements")
+    ap.add_argument("--profile-render", action="store_true",
+                    help="only render the workload (warmup + steps launches, default launch), for ncu")
+    ap.add_argument("--accel", action="store_true", help="with --profile-render: through the sphere hierarchy")
     ap.add_argument("--profile-batch", action="store_true",
                     help="only launch the 64-scene batch graph --warmup + --steps times (a profiling target)")
     args = ap.parse_args(argv)
@@ -531,6 +552,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.profile_batch:
         return profile_batch(args)
+    if args.profile_render:
+        return profile_render(args)
     rec = run_reference(args) if args.impl == "reference" else run_ours(args)
     if rec is not None:
         print(json.dumps(rec), flush=True)

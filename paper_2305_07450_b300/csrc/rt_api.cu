@@ -59,10 +59,11 @@ static SceneView view_of(const rt_scene* s) {
 // One thread per pixel.  The CTA covers block_x x block_y pixels; warp w covers an
 // 8 x 4 patch (lanes 0..7 = one row), so that a warp's primary and shadow rays
 // are coherent.  The scene header and geometry table are staged in shared memory
-// once per CTA.  Register budget 96 (5 CTAs of 128 threads per SM): measured
-// fastest on B300 among 96 / 104 / 128 and the allocator's own choice.
+// once per CTA.  Register budget 80 (6 CTAs of 128 threads per SM): measured on
+// B300 at 4K as 16.05 ms against 16.25 (96), 16.01 (72), 16.02 (64) and slower
+// at 104 / 112 / 128; the spills it causes sit outside the sphere loops.
 template <bool HITREC, bool CH>
-__global__ void __maxnreg__(96) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
+__global__ void __maxnreg__(80) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                      size_t pitch, float* __restrict__ hr, size_t hr_plane,
                                                      int staging, int block_x, int block_y) {
     extern __shared__ __align__(128) unsigned char smem[];

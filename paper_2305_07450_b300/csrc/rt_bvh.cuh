@@ -8,8 +8,9 @@
 // Why nothing is culled.  Boxes hold their spheres' exact extents (rounded outward
 // on the host).  A sphere the FP32 test accepts at parameter t has its point o + t d
 // within r + 26u M of the centre (u = 2^-24, M = |o|_inf + R, R the largest
-// |c|_inf + r of the scene), and the FP32 slab distances are within 5u M / |d_axis|
-// of the exact ones.  Every box is therefore widened, per ray, by
+// |c|_inf + r of the scene), and the FP32 slab parameters are within 5u M / |d_axis|
+// of the exact ones (d the ray direction, or the vector V of a shadow segment
+// o + u V, u in [0, 1]).  Every box is therefore widened, per ray, by
 // delta = 2^-16 M = 256u M per side, eight times what the two bounds need; the box
 // then starts before t and ends after it, in FP32 too.
 #pragma once
@@ -190,13 +191,13 @@ __device__ __forceinline__ void closest_bvh(const float4* __restrict__ geo, cons
     }
 }
 
-// Any sphere blocking the segment o + s dir, s in [0, dist] (o + u V, u in [0, 1],
-// for the sphere test): the OR of the brute-force predicate over the spheres of the
-// entered leaves; the first blocker ends the walk.
-__device__ __forceinline__ bool occluded_bvh(const float4* __restrict__ geo, const BvhView& bv, f3 o, f3 dir,
-                                             float dist, f3 w, f3 nv) {
+// Any sphere blocking the segment o + u V, u in [0, 1] (-V = nv, W = V / |V|^2):
+// the OR of the brute-force predicate over the spheres of the entered leaves (boxes
+// taken along V on [0, 1]); the first blocker ends the walk.
+__device__ __forceinline__ bool occluded_bvh(const float4* __restrict__ geo, const BvhView& bv, f3 o, f3 w, f3 nv) {
     if (bv.n_nodes <= 0) return false;
-    const RayInv q = ray_inv(o, dir, bv.r_scene);
+    const float dist = 1.0f;
+    const RayInv q = ray_inv(o, scl(nv, -1.0f), bv.r_scene);
     int stack[kBvhStack];
     int sp = 0;
     int ref = 0;

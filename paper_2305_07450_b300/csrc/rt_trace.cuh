@@ -146,9 +146,10 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
 
 // ---------------------------------------------------------------- Section 3.6
 // Any-hit of R shadow segments that leave the same origin o (one shading point).
-// Segment r is o + u V_r, u in [0, 1], V_r = dist_r dir_r; it is blocked by a sphere
+// Segment r is o + u V_r, u in [0, 1], V_r = the light point minus the hit point
+// (so it ends at the light point displaced by the origin's offset); it is blocked by a sphere
 // iff its point closest to the centre lies inside the ball: u* = clamp(oc.W_r, 0,
-// 1) with W_r = dir_r / dist_r (the clamp is the saturation of the last FMA), and
+// 1) with W_r = V_r / |V_r|^2 (the clamp is the saturation of the last FMA), and
 // |oc - u* V_r|^2 - r^2 < 0.  That is the paper's "a root in (0, dist)" whenever
 // the light is outside the sphere (checked at upload), including origins inside a
 // sphere.  The sign bits of the pair's two results are OR-ed into a per-segment
@@ -194,16 +195,30 @@ __device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, u
     return __all_sync(mask, done);
 }
 
-// occ[r] enters true for unused slots (and leaves true for blocked segments).
+// Segment r is o + u V_r (u in [0, 1]) with -V_r = nv[r] and W_r = w[r].  occ[r]
+// enters true for unused slots (and leaves true for blocked segments).  The plane is
+// tested first: a segment it blocks enters the sphere loop as blocked (the verdict
+// is an OR, so the order does not matter).
 template <int R, bool CH, bool ACC = false>
-__device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, const f3 (&dir)[kShadowGroup],
-                                               const float (&dist)[kShadowGroup], const f3 (&w)[kShadowGroup], const f3 (&nv)[kShadowGroup],
-                                               bool (&occ)[kShadowGroup]) {
-    const int n = sc.hdr->ns_pad;
+__device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, const f3 (&w)[kShadowGroup],
+                                               const f3 (&nv)[kShadowGroup], bool (&occ)[kShadowGroup]) {
+    const SceneHdr& h = *sc.hdr;
+    if (h.has_plane) {
+        const f3 pn = xyz(h.plane_g);
+        const float num = -(dot(o, pn) + h.plane_g.w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            // root u = num / (V.n) in (0, 1)  <=>  same signs and |num| < |V.n|
+            const float den = -dot(nv[r], pn);
+            if (!occ[r] && den != 0.0f && num != 0.0f && ((num > 0.0f) == (den > 0.0f)) && fabsf(num) < fabsf(den))
+                occ[r] = true;
+        }
+    }
+    const int n = h.ns_pad;
     if constexpr (ACC) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (!occ[r]) occ[r] = occluded_bvh(sc.geo, sc.bvh, o, dir[r], dist[r], w[r], nv[r]);
+            if (!occ[r]) occ[r] = occluded_bvh(sc.geo, sc.bvh, o, w[r], nv[r]);
     } else {
         const unsigned mask = __activemask();
         const RayPair o2 = ray_pair(o, mk3(0.f, 0.f, 0.f));
@@ -235,19 +250,6 @@ __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, cons
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) occ[r] = (acc[r] >> 31) != 0;
-    }
-    const SceneHdr& h = *sc.hdr;
-    if (h.has_plane) {
-        const f3 pn = xyz(h.plane_g);
-        const float num = -(dot(o, pn) + h.plane_g.w);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            // t = num / den in (0, dist)  <=>  same signs and |num| < dist |den|
-            const float den = dot(dir[r], pn);
-            if (!occ[r] && den != 0.0f && num != 0.0f && ((num > 0.0f) == (den > 0.0f)) &&
-                fabsf(num) < dist[r] * fabsf(den))
-                occ[r] = true;
-        }
     }
 }
 
@@ -337,16 +339,13 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
         const int kr = min(kShadowGroup, total - done);
         const int R = (int)__reduce_max_sync(mask, (unsigned)kr);
         if (R == 0) break;
-        f3 dir[kShadowGroup], sw[kShadowGroup], snv[kShadowGroup];  // direction, W and -V of each segment
-        float dist[kShadowGroup];
+        f3 sw[kShadowGroup], snv[kShadowGroup];  // W and -V of each segment
         bool occ[kShadowGroup];
         int l = cl, s = cs;
 #pragma unroll
         for (int j = 0; j < kShadowGroup; ++j) {
-            dir[j] = mk3(0.f, 1.f, 0.f);
             sw[j] = mk3(0.f, 0.f, 0.f);
             snv[j] = mk3(0.f, 0.f, 0.f);
-            dist[j] = 0.0f;
             occ[j] = true;
             if (j < kr) {
                 const float4 Lp = h.light_p[l];
@@ -354,9 +353,10 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
                 const int nr = rays_of_light(fr, Ls);
                 const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
                                                                    : xyz(Lp);
-                dir[j] = normalize_rn(sub(sub(X, p), p_lo), &dist[j]);
-                sw[j] = scl(dir[j], __frcp_rn(dist[j]));
-                snv[j] = scl(dir[j], -dist[j]);
+                // V = X - p (p as hi + lo), W = V / |V|^2
+                const f3 V = sub(sub(X, p), p_lo);
+                sw[j] = scl(V, __frcp_rn(dot(V, V)));
+                snv[j] = scl(V, -1.0f);
                 occ[j] = false;
                 if (++s == nr) {
                     s = 0;
@@ -366,13 +366,13 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
             }
         }
         if (kShadowGroup <= 1 || R == 1) {
-            occluded_group<1, CH, ACC>(sc, po, dir, dist, sw, snv, occ);
+            occluded_group<1, CH, ACC>(sc, po, sw, snv, occ);
         } else if (kShadowGroup == 2 || R == 2) {
-            occluded_group<(kShadowGroup < 2 ? 1 : 2), CH, ACC>(sc, po, dir, dist, sw, snv, occ);
+            occluded_group<(kShadowGroup < 2 ? 1 : 2), CH, ACC>(sc, po, sw, snv, occ);
         } else if (kShadowGroup == 3 || R == 3) {
-            occluded_group<(kShadowGroup < 3 ? 1 : 3), CH, ACC>(sc, po, dir, dist, sw, snv, occ);
+            occluded_group<(kShadowGroup < 3 ? 1 : 3), CH, ACC>(sc, po, sw, snv, occ);
         } else {
-            occluded_group<(kShadowGroup < 4 ? 1 : 4), CH, ACC>(sc, po, dir, dist, sw, snv, occ);
+            occluded_group<(kShadowGroup < 4 ? 1 : 4), CH, ACC>(sc, po, sw, snv, occ);
         }
         // attribute the results to their lights in the same order
 #pragma unroll
