@@ -44,6 +44,7 @@ class OrcIn(C.Structure):
         ("ambient", C.c_double), ("eps", C.c_double), ("scene_scale", C.c_double),
         ("seed", C.c_uint64), ("refl_coupled", C.c_int), ("pad2_", C.c_int),
         ("max_reflectivity", C.c_double),
+        ("sky", C.POINTER(C.c_float)), ("sky_w", C.c_int), ("sky_h", C.c_int),
     ]
 
 
@@ -80,6 +81,10 @@ def _bind(L):
     L.orc_occluded.restype = C.c_int
     L.orc_light_samples.argtypes = [C.POINTER(OrcIn), C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
     L.orc_light_samples.restype = C.c_int
+    L.orc_sky.argtypes = [C.POINTER(C.c_float), C.c_int, C.c_int, dp, dp]
+    L.orc_sky.restype = C.c_int
+    L.orc_verlet.argtypes = [C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double, C.c_int]
+    L.orc_verlet.restype = C.c_int
     return L
 
 
@@ -118,6 +123,11 @@ class _In:
         s.seed = int(params.seed) & 0xFFFFFFFFFFFFFFFF
         s.refl_coupled = int(getattr(params, "refl_coupled", 0))
         s.max_reflectivity = float(getattr(params, "max_reflectivity", 0.0))
+        sky = getattr(scene, "sky", None)
+        if sky is not None:
+            self.sky = np.ascontiguousarray(sky, dtype=np.float32)
+            s.sky = _fp(self.sky)
+            s.sky_h, s.sky_w = int(self.sky.shape[0]), int(self.sky.shape[1])
         self.s = s
 
 
@@ -252,6 +262,29 @@ def light_samples(scene, camera, params, l, x, y, k, p=(0.0, 0.0, 0.0)) -> np.nd
     if n < 0:
         raise ValueError("bad input")
     return out[:n].copy()
+
+
+def sky(tex, d) -> np.ndarray:
+    """Sky colour (RGB) of direction d for an [H, W, 4] FP32 panorama."""
+    t = np.ascontiguousarray(tex, dtype=np.float32)
+    dd = np.ascontiguousarray(d, np.float64)
+    out = np.zeros(3, np.float64)
+    if lib().orc_sky(_fp(t), int(t.shape[1]), int(t.shape[0]), _dp(dd), _dp(out)):
+        raise ValueError("bad input")
+    return out
+
+
+def verlet(pos, prev, radius, plane, dt: float, g: float, e: float, steps: int):
+    """Position-Verlet physics with ground contact: returns (pos, prev) [n, 3] after
+    `steps` steps (FP64); plane = (nx, ny, nz, d) or None."""
+    p = np.array(pos, np.float64, copy=True).reshape(-1, 3)
+    q = np.array(prev, np.float64, copy=True).reshape(-1, 3)
+    r = np.ascontiguousarray(radius, np.float64).reshape(-1)
+    pl = None if plane is None else np.ascontiguousarray(np.asarray(plane, np.float64)[:4])
+    if lib().orc_verlet(p.shape[0], _dp(p), _dp(q), _dp(r), _dp(pl) if pl is not None else None,
+                        float(dt), float(g), float(e), int(steps)):
+        raise ValueError("bad input")
+    return p, q
 
 
 class using_library:

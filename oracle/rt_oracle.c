@@ -58,6 +58,8 @@ typedef struct {
     int refl_coupled;       /* 1: reflection ratio = spec_exp / max_reflectivity   */
     int pad2_;
     double max_reflectivity;
+    const float *sky;       /* [sky_h][sky_w][4] RGBA panorama, or NULL (black)    */
+    int sky_w, sky_h;
 } orc_in;
 
 /* One primitive promoted to FP64.  For the plane, g = normal and r = d. */
@@ -79,6 +81,8 @@ typedef struct {
     int W, H, D, nsamp, model;
     double ka, eps, S;
     uint32_t key[2];
+    const float *sky;
+    int sky_w, sky_h;
 } Ctx;
 
 typedef struct {
@@ -427,8 +431,45 @@ static void hit_geometry(const Ctx *cx, int id, v3 o, v3 d, double t, v3 *p, v3 
     if (dot(*n, d) > 0.0) *n = scl(*n, -1.0);
 }
 
-/* Section 3.7.1, recursive reflections, written literally: a miss is black; at the
- * bounce limit the hit is shaded with its own colour; otherwise the colour is mixed
+/* --------------------------------------------------------------- Section 3.8 sky */
+/* A ray that leaves the scene shows the sky: the paper samples an HDR panorama by
+ * UV mapping of the ray direction (Section 3.8, skybox; Section 3.9 skybox
+ * argument).  Reading: an equirectangular panorama of W x H RGBA texels stored
+ * row-major from the top row, with the spherical UV mapping of a unit direction
+ *   u = 1/2 + atan2(d_z, d_x) / (2 pi),   v = 1/2 - asin(d_y) / pi,
+ * and bilinear interpolation between texel centres ((i + 1/2) / W, (j + 1/2) / H),
+ * wrapping around in u and clamped to the first and last rows in v. */
+static double sky_texel(const float *tex, int W, int i, int j, int c) { return tex[((size_t)j * W + i) * 4 + c]; }
+
+static void sky_lookup(const float *tex, int W, int H, v3 d, double out[3])
+{
+    const double dy = fmax(-1.0, fmin(1.0, d.y / len(d)));
+    const double u = 0.5 + atan2(d.z, d.x) / (2.0 * M_PI);
+    const double v = 0.5 - asin(dy) / M_PI;
+    const double x = u * W - 0.5, y = v * H - 0.5;
+    const double x0 = floor(x), y0 = floor(y);
+    const double fx = x - x0, fy = y - y0;
+    int i0 = (int)fmod(x0, (double)W);
+    if (i0 < 0) i0 += W;
+    const int i1 = (i0 + 1) % W;
+    int j0 = (int)y0, j1 = (int)y0 + 1;
+    j0 = j0 < 0 ? 0 : (j0 > H - 1 ? H - 1 : j0);
+    j1 = j1 < 0 ? 0 : (j1 > H - 1 ? H - 1 : j1);
+    for (int c = 0; c < 3; ++c) {
+        const double top = (1.0 - fx) * sky_texel(tex, W, i0, j0, c) + fx * sky_texel(tex, W, i1, j0, c);
+        const double bot = (1.0 - fx) * sky_texel(tex, W, i0, j1, c) + fx * sky_texel(tex, W, i1, j1, c);
+        out[c] = (1.0 - fy) * top + fy * bot;
+    }
+}
+
+static void miss_color(const Ctx *cx, v3 d, double out[3])
+{
+    if (cx->sky) sky_lookup(cx->sky, cx->sky_w, cx->sky_h, d, out);
+    else out[0] = out[1] = out[2] = 0.0;
+}
+
+/* Section 3.7.1, recursive reflections, written literally: a miss is black (or the
+ * sky, Section 3.8, when one is given); at the bounce limit the hit is shaded with its own colour; otherwise the colour is mixed
  * with the reflected colour by the reflection ratio and the mix is shaded.  The
  * reflection ratio is the per-object reflectivity field (reading: the paper derives
  * it as reflectivity / MAX_REFLECTIVITY with the same field as the Phong exponent;
@@ -441,7 +482,7 @@ static void trace_recursive(Path *P, v3 o, v3 d, int depth, int k, int origin, d
     double t;
     P->origin = origin;
     int id = closest_hit(P, o, d, &t);
-    if (id < 0) { out[0] = out[1] = out[2] = 0.0; return; }
+    if (id < 0) { miss_color(cx, d, out); return; }
     const Prim *m = &cx->prim[id];
     v3 p, n;
     hit_geometry(cx, id, o, d, t, &p, &n);
@@ -464,7 +505,8 @@ static void trace_recursive(Path *P, v3 o, v3 d, int depth, int k, int origin, d
 /* The same definition unrolled forward (Section 3.7.2 replaces the recursion by a
  * loop).  Since shade(c) = c A + S is affine, with throughput T_0 = 1:
  *   k < D : out += T_k ((1 - rho_k) A_k c_k + S_k),  T_{k+1} = T_k rho_k A_k
- *   k = D : out += T_D (A_D c_D + S_D);  a miss adds nothing and ends the path. */
+ *   k = D : out += T_D (A_D c_D + S_D);  a miss at bounce k adds T_k sky(d_k) (nothing
+ *   without a sky) and ends the path. */
 static void trace_forward(Path *P, v3 o, v3 d, double out[3])
 {
     const Ctx *cx = P->cx;
@@ -475,7 +517,12 @@ static void trace_forward(Path *P, v3 o, v3 d, double out[3])
         P->cnt[k == 0 ? C_PRIMARY : C_REFLECT] += 1;
         double t;
         int id = closest_hit(P, o, d, &t);
-        if (id < 0) break;
+        if (id < 0) {
+            double sk[3];
+            miss_color(cx, d, sk);
+            for (int c = 0; c < 3; ++c) out[c] += T * sk[c];
+            break;
+        }
         P->origin = id;
         const Prim *m = &cx->prim[id];
         v3 p, n;
@@ -553,6 +600,10 @@ static int build_ctx(const orc_in *in, Ctx *cx)
     cx->S = in->scene_scale;
     cx->key[0] = (uint32_t)(in->seed & 0xffffffffu);
     cx->key[1] = (uint32_t)(in->seed >> 32);
+    if (in->sky && (in->sky_w <= 0 || in->sky_h <= 0)) { free(cx->prim); free(cx->light); return -1; }
+    cx->sky = in->sky;
+    cx->sky_w = in->sky_w;
+    cx->sky_h = in->sky_h;
     return 0;
 }
 
@@ -680,4 +731,52 @@ ORC_API int orc_light_samples(const orc_in *in, int l, int x, int y, int k, cons
     free(cx.prim);
     free(cx.light);
     return n;
+}
+
+/* The sky colour of one direction (Section 3.8 reading above). */
+ORC_API int orc_sky(const float *tex, int w, int h, const double *d, double *rgb)
+{
+    if (!tex || w <= 0 || h <= 0) return -1;
+    sky_lookup(tex, w, h, V(d[0], d[1], d[2]), rgb);
+    return 0;
+}
+
+/* ----------------------------------------------------------- Section 3.8 physics */
+/* The physics system moves the bodies by Verlet integration (Section 3.8; the
+ * bodies' positions are streamed in every frame, Section 3.9).  Reading: position
+ * Verlet, x_{n+1} = x_n + (x_n - x_{n-1}) + a dt^2 with a = (0, -g, 0), from the
+ * current and the previous positions; contact with the ground plane n.x + pd = 0
+ * (plane NULL: none): a sphere that crosses it is moved back along n until it
+ * touches it, and the step's velocity v = x_{n+1} - x_n (taken before the move)
+ * loses its normal component into the plane if that is at most one step of gravity
+ * (g dt^2: resting contact), else has it reversed and scaled by the restitution e;
+ * the previous position is set to x_{n+1} - v so that the next step continues with
+ * that velocity.  pos and prev are [n][3], updated in place over `steps` steps. */
+ORC_API int orc_verlet(int n, double *pos, double *prev, const double *radius, const double *plane, double dt,
+                       double g, double e, int steps)
+{
+    if (n < 0 || steps < 0 || (n && (!pos || !prev || !radius))) return -1;
+    const double gdt2 = g * dt * dt;
+    for (int s = 0; s < steps; ++s) {
+        for (int i = 0; i < n; ++i) {
+            const v3 x = V(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]);
+            const v3 xp = V(prev[3 * i], prev[3 * i + 1], prev[3 * i + 2]);
+            v3 xn = add(add(x, sub(x, xp)), V(0.0, -gdt2, 0.0));
+            v3 xq = x;
+            if (plane) {
+                const v3 nn = V(plane[0], plane[1], plane[2]);
+                const double sd = dot(nn, xn) + plane[3] - radius[i];
+                if (sd < 0.0) {
+                    v3 v = sub(xn, x);
+                    xn = sub(xn, scl(nn, sd));
+                    const double vn = dot(v, nn);
+                    if (vn < 0.0) v = sub(v, scl(nn, -vn <= gdt2 ? vn : (1.0 + e) * vn));
+                    xq = sub(xn, v);
+                }
+            }
+            pos[3 * i] = xn.x; pos[3 * i + 1] = xn.y; pos[3 * i + 2] = xn.z;
+            prev[3 * i] = xq.x; prev[3 * i + 1] = xq.y; prev[3 * i + 2] = xq.z;
+        }
+    }
+    return 0;
 }

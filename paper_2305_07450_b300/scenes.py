@@ -54,6 +54,7 @@ class Scene:
     plane: np.ndarray | None       # float32 [10] or None
     lights: np.ndarray             # float32 [L, 8]
     scale: float = 1.0             # the box scale s of the generator
+    sky: np.ndarray | None = None  # float32 [H, W, 4] equirectangular panorama (None: black)
 
     @property
     def scene_scale(self) -> float:
@@ -231,6 +232,58 @@ def diff_512() -> Workload:
     sc = random_scene(5, 32, 2, s)
     return Workload("512x512_32sph_2pt_d2_f32", sc, default_camera(s),
                     _params(sc, width=512, height=512, max_depth=2, out_format=OUT_F32, seed=5))
+
+
+def sky_texture(seed: int = 7, width: int = 512, height: int = 256) -> np.ndarray:
+    """A seeded synthetic HDR panorama standing in for the paper's sky image (Section
+    3.8; the image itself is not available): float32 [height, width, 4], rows from
+    the top (latitude +90 deg) down, columns over longitude.  A zenith-to-horizon
+    blue gradient, a darker ground below the horizon, low-frequency cloud bands
+    (random harmonics in longitude and latitude) and one sun of HDR intensity 6 at
+    a random azimuth and elevation 20-60 deg; alpha 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lat = (0.5 - (np.arange(height) + 0.5) / height) * np.pi          # +pi/2 .. -pi/2
+    lon = ((np.arange(width) + 0.5) / width - 0.5) * 2.0 * np.pi       # -pi .. pi
+    LON, LAT = np.meshgrid(lon, lat)
+    up = np.clip(np.sin(LAT), 0.0, 1.0)[..., None]
+    zenith, horizon, ground = np.array([0.22, 0.42, 0.85]), np.array([0.85, 0.82, 0.78]), np.array([0.32, 0.29, 0.25])
+    col = np.where(LAT[..., None] >= 0, horizon + (zenith - horizon) * up ** 0.6, ground)
+    clouds = np.zeros_like(LAT)
+    for _ in range(6):
+        kx, ky = rng.integers(1, 6), rng.integers(1, 4)
+        clouds += rng.uniform(0.2, 1.0) * np.sin(kx * LON + rng.uniform(0, 2 * np.pi)) * \
+            np.cos(ky * LAT * 2 + rng.uniform(0, 2 * np.pi))
+    clouds = np.clip(clouds / 3.0, 0.0, 1.0) * (LAT > 0)
+    col = col * (1.0 - 0.5 * clouds[..., None]) + 0.9 * clouds[..., None] * 0.5
+    az, el = rng.uniform(-np.pi, np.pi), rng.uniform(np.radians(20), np.radians(60))
+    sun = np.array([np.cos(el) * np.cos(az), np.sin(el), np.cos(el) * np.sin(az)])
+    dirs = np.stack([np.cos(LAT) * np.cos(LON), np.sin(LAT), np.cos(LAT) * np.sin(LON)], -1)
+    cosang = np.clip(dirs @ sun, -1.0, 1.0)
+    col = col + 6.0 * np.exp(-(1.0 - cosang) / 2e-4)[..., None] * np.array([1.0, 0.95, 0.85])
+    out = np.ones((height, width, 4), np.float32)
+    out[..., :3] = col
+    return f32(out)
+
+
+def animated_scene(width: int = 1280, height: int = 720) -> tuple[Workload, np.ndarray]:
+    """The animated loop: the paper-structure scene (five spheres, one spherical
+    light, plane, Blinn-Phong, hard shadows, bounce limit 1: the paper's real-time
+    setting) with the synthetic sky, its spheres lifted 1-3 units above their seeded
+    places and given a seeded horizontal velocity, to fall and bounce under Verlet
+    physics (Section 3.8).  Returns the workload and the previous positions [N, 3]
+    (one step of 1/60 s back along the velocity)."""
+    w = paper_scene(width, height, 1, 1)
+    rng = np.random.Generator(np.random.PCG64(42))
+    sph = w.scene.spheres.astype(np.float64).copy()
+    n = sph.shape[0]
+    sph[:, 1] += rng.uniform(1.0, 3.0, n)
+    vel = np.zeros((n, 3))
+    vel[:, 0], vel[:, 2] = rng.uniform(-1.0, 1.0, n), rng.uniform(-1.0, 1.0, n)
+    prev = sph[:, :3] - vel / 60.0
+    w.scene = Scene(spheres=f32(sph), plane=w.scene.plane, lights=w.scene.lights, scale=w.scene.scale,
+                    sky=sky_texture())
+    w.name = f"animated_{width}x{height}_5sph_1sphlight_sky_d1_rgba8"
+    return w, f32(prev)
 
 
 def perturbed_target(w: Workload, seed: int = 6) -> Scene:

@@ -626,4 +626,142 @@ def pin_vogel_sunflower(orc):
     golden = min(float(step[0]), 360.0 - float(step[0]))      # orientation-free
     assert abs(golden - float(deg)) < 10.0 ** -int(decimals), golden
 
+# ----------------------------------------------------------------- sky (NEXT-3)
+def _sky_tex(seed, W=16, H=8):
+    t = np.random.default_rng(seed).random((H, W, 4)).astype(np.float32)
+    t[..., 3] = 1.0
+    return t
+
+
+def _unit(rng, n):
+    d = rng.normal(size=(n, 3))
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def pin_sky_invariants(orc):
+    """Section 3.8 sky, equirectangular UV mapping (u = longitude, v = latitude from
+    the top), bilinear between texel centres.  Checked by properties only: a constant
+    panorama is constant; turning the direction by one texel of longitude (2 pi / W
+    about y) equals shifting the panorama by one column; flipping the latitude
+    equals flipping the rows; a panorama symmetric under column mirror i -> W-1-i
+    gives z-mirror symmetric colours (this fixes the half-texel offset); the
+    cardinal directions of the convention u = 1/2 + atan2(d_z, d_x) / 2 pi land on
+    the columns it names; a panorama that varies only by row gives its top row
+    straight up and the mean of the two middle rows on the horizon."""
+    rng = np.random.default_rng(5)
+    W, H = 16, 8
+    const = np.ones((H, W, 4), np.float32) * np.float32(0.3)
+    for d in _unit(rng, 20):
+        assert np.allclose(orc.sky(const, d), 0.3, atol=1e-7)
+    T = _sky_tex(1, W, H)
+    shifted = np.ascontiguousarray(np.roll(T, -1, axis=1))
+    fl = np.ascontiguousarray(T[::-1])
+    mir = np.ascontiguousarray(0.5 * (T + T[:, ::-1]))
+    a = 2 * np.pi / W
+    rot = np.array([[math.cos(a), 0, -math.sin(a)], [0, 1, 0], [math.sin(a), 0, math.cos(a)]])
+    for d in _unit(rng, 40):
+        # rot turns atan2(z, x) by +a
+        assert np.allclose(orc.sky(T, rot @ d), orc.sky(shifted, d), atol=1e-9), d
+        assert np.allclose(orc.sky(T, d * [1, -1, 1]), orc.sky(fl, d), atol=1e-9), d
+        assert np.allclose(orc.sky(mir, d), orc.sky(mir, d * [1, 1, -1]), atol=1e-9), d
+    # columns by index, rows constant: longitude -> column
+    C = np.zeros((H, W, 4), np.float32)
+    C[..., 0] = np.arange(W, dtype=np.float32)[None, :]
+    for d, col in (((1, 0, 0), W / 2 - 0.5), ((0, 0, 1), 3 * W / 4 - 0.5), ((0, 0, -1), W / 4 - 0.5)):
+        assert abs(orc.sky(C, d)[0] - col) < 1e-9, (d, orc.sky(C, d))
+    # -x is the seam: halfway between the last and the first column
+    assert abs(orc.sky(C, (-1, 1e-12, -1e-15))[0] - 0.5 * (W - 1)) < 1e-6
+    R = np.zeros((H, W, 4), np.float32)
+    R[..., 1] = np.arange(H, dtype=np.float32)[:, None]
+    assert abs(orc.sky(R, (0, 1, 0))[1] - 0.0) < 1e-12 and abs(orc.sky(R, (0, -1, 0))[1] - (H - 1)) < 1e-12
+    assert abs(orc.sky(R, (0.3, 0.0, -0.7))[1] - (H / 2 - 0.5)) < 1e-9
+    # interpolation weights: the stored row (column) index rises strictly as the
+    # direction sweeps down in latitude (east in longitude, away from the seam)
+    lat = np.radians(np.linspace(75, -75, 301))
+    rows = [orc.sky(R, (math.cos(b) * 0.6, math.sin(b), math.cos(b) * 0.8))[1] for b in lat]
+    assert np.all(np.diff(rows) > 0), "row weights"
+    lon = np.radians(np.linspace(-160, 160, 301))
+    cols = [orc.sky(C, (math.cos(l), 0.2, math.sin(l)))[0] for l in lon]
+    assert np.all(np.diff(cols) > 0), "column weights"
+
+
+def pin_sky_on_misses(orc):
+    """A ray that leaves the scene shows the sky (Section 3.8); through the bounce
+    recursion (Section 3.7.1) a perfect mirror sphere (reflectivity 1, no lights)
+    shows k_a times the sky in the mirror direction, computed here from the
+    closed-form hit point of the sphere."""
+    T = _sky_tex(2, 32, 16)
+    cam = (0, 0, -5, 0, 0, 60)
+    sc, c, p = mk(camera=cam, W=8, H=6)
+    sc.sky = T
+    for x, y in ((0, 0), (3, 2), (7, 5)):
+        o, d = orc.primary_ray(sc, c, p, x, y)
+        assert np.allclose(pix(orc, sc, c, p, x, y), orc.sky(T, d), atol=1e-12)
+    ka = 0.25
+    sc, c, p = mk(spheres=[sphere((0, 0, 0), 1.0, albedo=(0.9, 0.1, 0.4), refl=1.0)], camera=cam, W=9, H=9,
+                  D=1, ka=ka)
+    sc.sky = T
+    for x, y in ((4, 4), (3, 5), (5, 3)):
+        o, d = orc.primary_ray(sc, c, p, x, y)
+        b = float(np.dot(o, d))
+        disc = b * b - (float(np.dot(o, o)) - 1.0)
+        assert disc > 0
+        t = -b - math.sqrt(disc)
+        n = o + t * d                                   # unit sphere at the origin
+        r = d - 2 * np.dot(d, n) * n
+        want = ka * orc.sky(T, r)
+        for mode in ("forward", "recursive"):
+            got = orc.trace(sc, c, p, np.array([[x, y]], np.int32), mode=mode, threads=1)["rgb"][0]
+            assert np.allclose(got, want, atol=1e-9), (mode, got, want)
+
+
+# ------------------------------------------------------------- physics (NEXT-3)
+def pin_verlet_free_fall(orc):
+    """Position Verlet is exact for constant acceleration: from x_0 and x_{-1} =
+    x_0 - v_0 dt, x_n = x_0 + n v_0 dt - g dt^2 n (n + 1) / 2 (y), with no plane."""
+    rng = np.random.default_rng(3)
+    x0 = rng.uniform(-5, 5, (6, 3))
+    v0 = rng.uniform(-2, 2, (6, 3))
+    dt, g, n = 1.0 / 60.0, 9.81, 240
+    pos, prev = orc.verlet(x0, x0 - v0 * dt, np.ones(6), None, dt, g, 0.5, n)
+    want = x0 + n * v0 * dt
+    want[:, 1] -= g * dt * dt * n * (n + 1) / 2
+    assert np.allclose(pos, want, rtol=0, atol=1e-9), np.abs(pos - want).max()
+    assert np.allclose(pos - prev, v0 * dt + np.array([0, -g * dt * dt * n, 0]), atol=1e-9)
+
+
+def pin_verlet_ground_contact(orc):
+    """Contact with the ground plane: a resting sphere stays exactly at rest; with
+    restitution 0 a dropped sphere ends touching the plane and keeps its horizontal
+    velocity; with restitution 1 it bounces back to within a step of its drop
+    height; a tilted plane leaves the sphere touching it after the contact step."""
+    dt, g = 1.0 / 120.0, 9.81
+    plane = (0.0, 1.0, 0.0, 0.0)
+    r = np.array([0.5])
+    x = np.array([[1.0, 0.5, -2.0]])
+    pos, prev = orc.verlet(x, x, r, plane, dt, g, 0.7, 1000)
+    assert np.array_equal(pos, x) and np.array_equal(prev, x)
+    h = 3.0
+    x = np.array([[0.0, h, 0.0]])
+    vx = 0.4
+    pos, prev = orc.verlet(x, x - [[vx * dt, 0, 0]], r, plane, dt, g, 0.0, 300)
+    assert abs(pos[0, 1] - 0.5) < 1e-12 and abs(pos[0, 1] - prev[0, 1]) < 1e-12
+    assert abs((pos[0, 0] - prev[0, 0]) - vx * dt) < 1e-12
+    pos, prev = x.copy(), x.copy()
+    top, seen_ground = 0.0, False
+    for _ in range(400):                                  # ~ two bounces
+        pos, prev = orc.verlet(pos, prev, r, plane, dt, g, 1.0, 1)
+        if pos[0, 1] < 0.5 + 1e-9:
+            seen_ground = True
+        if seen_ground:
+            top = max(top, pos[0, 1])
+    v_impact = math.sqrt(2 * g * (h - 0.5))
+    assert seen_ground and abs(top - h) < 2 * v_impact * dt, (top, h)
+    nrm = np.array([0.3, 1.0, -0.2]) / np.linalg.norm([0.3, 1.0, -0.2])
+    tilted = (*nrm, 0.4)
+    x = np.array([[0.2, 1.0, 0.1]]) - nrm * (np.dot(nrm, [0.2, 1.0, 0.1]) + 0.4 - 0.5 - 1e-3)
+    pos, prev = orc.verlet(x, x + nrm * 0.05, r, tilted, dt, g, 0.5, 1)
+    assert abs(np.dot(nrm, pos[0]) + 0.4 - 0.5) < 1e-12
+
+
 PINS = {k: v for k, v in globals().items() if k.startswith("pin_")}

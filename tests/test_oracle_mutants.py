@@ -18,6 +18,7 @@ ORDER = ["pin_ndc_worked_example", "pin_ndc_shorter_side_spans_unit_square",
          "pin_margin_grazing", "pin_counters", "pin_area_samples_stratified", "pin_vogel_sunflower",
          "pin_reflection_mixing_closed_form", "pin_coupled_reflectivity",
          "pin_depth_reductions", "pin_area_light", "pin_mirror_symmetry",
+         "pin_sky_invariants", "pin_sky_on_misses", "pin_verlet_free_fall", "pin_verlet_ground_contact",
          "pin_recursion_equals_loop", "pin_occlusion_brute_force",
          "pin_closest_hit_brute_force"]
 
@@ -62,6 +63,24 @@ MUTANTS = {
                             "double r = 2.0 * L->srad * sqrt((double)i / (double)n);"),
     "vogel_angle": ("double phi = M_PI * (3.0 - sqrt(5.0));", "double phi = M_PI * (3.0 - sqrt(3.0));"),
     "coupled_uncapped": ("p->rho = fmin(p->ex / in->max_reflectivity, 1.0);", "p->rho = p->ex / in->max_reflectivity;"),
+    "sky_u_sign": ("const double u = 0.5 + atan2(d.z, d.x) / (2.0 * M_PI);",
+                   "const double u = 0.5 + atan2(-d.z, d.x) / (2.0 * M_PI);"),
+    "sky_u_full_turn_half": ("const double u = 0.5 + atan2(d.z, d.x) / (2.0 * M_PI);",
+                             "const double u = 0.5 + atan2(d.z, d.x) / M_PI;"),
+    "sky_no_half_texel": ("const double x = u * W - 0.5, y = v * H - 0.5;",
+                          "const double x = u * W, y = v * H - 0.5;"),
+    "sky_v_flipped": ("const double v = 0.5 - asin(dy) / M_PI;", "const double v = 0.5 + asin(dy) / M_PI;"),
+    "sky_u_clamped": ("const int i1 = (i0 + 1) % W;", "const int i1 = i0 + 1 < W ? i0 + 1 : W - 1;"),
+    "sky_lerp_swapped": ("out[c] = (1.0 - fy) * top + fy * bot;", "out[c] = fy * top + (1.0 - fy) * bot;"),
+    "miss_black_forward": ("for (int c = 0; c < 3; ++c) out[c] += T * sk[c];", ""),
+    "miss_black_recursive": ("if (id < 0) { miss_color(cx, d, out); return; }",
+                             "if (id < 0) { out[0] = out[1] = out[2] = 0.0; return; }"),
+    "verlet_no_inertia": ("v3 xn = add(add(x, sub(x, xp)), V(0.0, -gdt2, 0.0));", "v3 xn = add(x, V(0.0, -gdt2, 0.0));"),
+    "verlet_half_gravity": ("const double gdt2 = g * dt * dt;", "const double gdt2 = 0.5 * g * dt * dt;"),
+    "verlet_restitution_ignored": ("(1.0 + e) * vn", "2.0 * vn"),
+    "verlet_no_pushout": ("xn = sub(xn, scl(nn, sd));", ""),
+    "verlet_no_rest_contact": ("-vn <= gdt2 ? vn : (1.0 + e) * vn", "(1.0 + e) * vn"),
+    "verlet_prev_not_reset": ("xq = sub(xn, v);", "xq = x;"),
 }
 
 
