@@ -364,9 +364,40 @@ def extras(args, dev, stream):
     for d in dss:
         d.close()
     out["bvh"] = bvh_extra(dev, stream)
+    out["animated"] = animated_extra(dev, stream)
     out["fwd_adjoint"] = fwd_adjoint(dev, stream)
     out["paper_scene"] = paper_scene(dev, stream)
     return out
+
+
+def animated_extra(dev, stream):
+    """The animated loop (Sections 3.8-3.9, the paper's interactive setting: hard
+    shadows, bounce limit 1, five spheres, a light, the plane, a sky panorama):
+    every frame a Verlet step on the device, the scene update from device records,
+    the render and the pixels read back to pinned host memory, the host waiting for
+    each frame as a display loop does.  End-to-end frames/s by host clock over 120
+    frames; the device time of one frame (physics + update + render) by events."""
+    import torch
+    from paper_2305_07450_b300 import animate
+    res = {"note": "paper's 234/152/45 frames/s (RTX 2060, GUI, its own scene and sky) are context, not a target"}
+    for W, H in ((1280, 720), (1920, 1080), (3840, 2160)):
+        w, prev = S.animated_scene(W, H)
+        an = animate.Animation(w, prev, stream=stream)
+        for _ in range(5):
+            an.step()
+        torch.cuda.synchronize()
+        n = 120
+        t0 = time.perf_counter()
+        for _ in range(n):
+            an.step(readback=True)
+            stream.synchronize()
+        e2e = n / (time.perf_counter() - t0)
+        ms_dev = _time_device(lambda: an.step(readback=False), stream, 60)
+        res[f"{W}x{H}"] = {"workload": w.name, "frames_per_s_end_to_end": e2e, "ms_device_frame": ms_dev,
+                           "d2h_bytes_per_frame": int(an.out.numel() * an.out.element_size()),
+                           "launches_per_frame": 3}
+        an.close()
+    return res
 
 
 def bvh_extra(dev, stream):

@@ -145,6 +145,40 @@ rt_status rt_scene_update(rt_scene *scene, const rt_scene_desc *desc, int32_t de
  * NULL is accepted. */
 rt_status rt_scene_free(rt_scene *scene);
 
+/* ---------------------------------------------------------------- sky and physics
+ * The paper's additional components (Section 3.8): an HDR sky panorama shown by
+ * rays that leave the scene, and a Verlet physics system that moves the bodies
+ * between frames (their positions are streamed in every frame, Section 3.9).  The
+ * paper's sky image is not available; any panorama can be given. */
+
+/* Give the scene a sky panorama, or remove it (texels NULL: misses are black).
+ *   texels: host array of height rows (the first row is straight up) of width RGBA
+ *           FP32 texels (A ignored), copied to the device before the call returns
+ *           (width, height in 1..16384; every value finite).
+ * A ray that leaves the scene at bounce k adds T_k sky(d) with the equirectangular
+ * UV mapping u = 1/2 + atan2(d_z, d_x) / (2 pi), v = 1/2 - asin(d_y) / pi and
+ * bilinear interpolation between texel centres, wrapping in u, clamped in v.
+ * Removing or resizing a sky synchronises the device.  rt_render_backward refuses
+ * scenes with a sky (RT_ERR_UNSUPPORTED). */
+rt_status rt_scene_set_sky(rt_scene *scene, const float *texels, int32_t width, int32_t height, void *stream);
+
+/* Advance n bodies by `steps` steps of position Verlet integration under gravity
+ * (0, -gravity, 0) with time step dt (one kernel launch on `stream`):
+ *   x' = x + (x - x_prev) + a dt^2;
+ * with a ground plane (plane: host [4] = nx, ny, nz, d of n.x + d = 0, |n| = 1; or
+ * NULL for none) a sphere that crosses it is moved back along n until it touches
+ * it, and the step's velocity component into the plane is dropped when it is at
+ * most 2 gravity dt^2 (resting contact), else reversed and scaled by restitution
+ * (0..1).
+ *   spheres_dev: device sphere records [n][10] (the rt_scene_desc layout); centres
+ *                (fields 0..2) are read and updated in place, radii (field 3) read.
+ *   prev_dev:    device [n][3] previous centres, updated in place.
+ * Feed the records to rt_scene_update(desc_on_device = 1) to render the new frame.
+ * Errors: RT_ERR_INVALID_ARG (counts, pointers, dt <= 0, restitution outside
+ * [0, 1], a non-unit plane normal). */
+rt_status rt_verlet_step(float *spheres_dev, float *prev_dev, int32_t n, const float *plane, float dt,
+                         float gravity, float restitution, int32_t steps, void *stream);
+
 /* ---------------------------------------------------------------- hierarchy
  * Bounding-volume hierarchy over the spheres: the spatial acceleration structure
  * the paper names as future work (Section 6); the paper's own kernel tests every

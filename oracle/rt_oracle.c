@@ -748,8 +748,10 @@ ORC_API int orc_sky(const float *tex, int w, int h, const double *d, double *rgb
  * current and the previous positions; contact with the ground plane n.x + pd = 0
  * (plane NULL: none): a sphere that crosses it is moved back along n until it
  * touches it, and the step's velocity v = x_{n+1} - x_n (taken before the move)
- * loses its normal component into the plane if that is at most one step of gravity
- * (g dt^2: resting contact), else has it reversed and scaled by the restitution e;
+ * loses its normal component into the plane if that is at most two steps of
+ * gravity (2 g dt^2: resting contact, whose component is one step of gravity; the
+ * factor keeps rounding from classifying rest as an impact), else has it reversed
+ * and scaled by the restitution e;
  * the previous position is set to x_{n+1} - v so that the next step continues with
  * that velocity.  pos and prev are [n][3], updated in place over `steps` steps. */
 ORC_API int orc_verlet(int n, double *pos, double *prev, const double *radius, const double *plane, double dt,
@@ -770,7 +772,7 @@ ORC_API int orc_verlet(int n, double *pos, double *prev, const double *radius, c
                     v3 v = sub(xn, x);
                     xn = sub(xn, scl(nn, sd));
                     const double vn = dot(v, nn);
-                    if (vn < 0.0) v = sub(v, scl(nn, -vn <= gdt2 ? vn : (1.0 + e) * vn));
+                    if (vn < 0.0) v = sub(v, scl(nn, -vn <= 2.0 * gdt2 ? vn : (1.0 + e) * vn));
                     xq = sub(xn, v);
                 }
             }

@@ -43,6 +43,9 @@ struct rt_scene {
     size_t bvh_cap = 0;
     cudaEvent_t bvh_copy_done = nullptr;
     rt_bvh_info bvh_info{};
+    // sky panorama (Section 3.8): sky_h rows of sky_w RGBA texels, or none
+    void* sky_dev = nullptr;
+    int sky_w = 0, sky_h = 0;
 };
 
 static SceneView view_of(const rt_scene* s) {
@@ -52,6 +55,9 @@ static SceneView view_of(const rt_scene* s) {
     v.geo = reinterpret_cast<const float4*>(b + sizeof(SceneHdr));
     v.mat = v.geo + s->ns_pad;
     v.mat2 = v.mat + s->ns_pad;
+    v.sky.tex = static_cast<const float4*>(s->sky_dev);
+    v.sky.w = s->sky_w;
+    v.sky.h = s->sky_h;
     return v;
 }
 
@@ -79,8 +85,8 @@ __global__ void __maxnreg__(80) rt_fwd_kernel(const SceneView sv, const Frame fr
     const int lane = threadIdx.x, warp = threadIdx.y;
     const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
     float4* tab = reinterpret_cast<float4*>(smem + sizeof(SceneHdr));
-    const StagedScene sc{hdr, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)warp * kChunk : nullptr, sv.mat,
-                         sv.mat2};
+    StagedScene sc{hdr, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)warp * kChunk : nullptr, sv.mat, sv.mat2};
+    sc.sky = sv.sky;
 
     const int wpr = block_x >> 3;
     const int x = fr.rx0 + blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
@@ -115,6 +121,7 @@ __global__ void __launch_bounds__(256) rt_fwd_bvh_kernel(const SceneView sv, con
     StagedScene sc{hdr, staged ? reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)) : sv.geo, sv.geo, nullptr,
                    sv.mat, sv.mat2};
     sc.bvh = bv;
+    sc.sky = sv.sky;
     if (staged) {
         sc.bvh.nodes = reinterpret_cast<const BvhNode*>(bvh_s);
         sc.bvh.prim = reinterpret_cast<const int32_t*>(bvh_s + (size_t)bv.n_nodes * sizeof(BvhNode));
@@ -167,6 +174,51 @@ __global__ void rt_pack_kernel(SceneView sv, int ns, const float* __restrict__ s
             h->light_s[l] = make_float4(f[4], f[5], 0.f, 0.f);
         }
     }
+}
+
+// Physics step of the animated loop (Section 3.8: the bodies move by Verlet
+// integration; their positions are streamed in every frame, Section 3.9).  One
+// thread per sphere, `steps` steps of position Verlet under gravity (0, -g, 0):
+// x' = x + (x - x_prev) + a dt^2; a sphere that crosses the ground plane
+// n.x + pd = 0 is moved back along n until it touches it, and the step velocity's
+// normal component into the plane is dropped when it is at most two steps of
+// gravity (resting contact has one), else reversed and scaled by the restitution e; the
+// previous position is set so that the next step carries that velocity.  The
+// centre is updated in place in the sphere record; prev holds x_prev [n][3].
+__global__ void rt_verlet_kernel(float* __restrict__ sph, float* __restrict__ prev, int n, float4 plane,
+                                 int has_plane, float dt, float g, float e, int steps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float* rec = sph + 10 * (size_t)i;
+    float* pv = prev + 3 * (size_t)i;
+    const float r = rec[3];
+    f3 x = mk3(rec[0], rec[1], rec[2]), xp = mk3(pv[0], pv[1], pv[2]);
+    const f3 nn = mk3(plane.x, plane.y, plane.z);
+    const float gdt2 = g * dt * dt;
+#pragma unroll 1
+    for (int s = 0; s < steps; ++s) {
+        f3 xn = add(x, sub(x, xp));
+        xn.y -= gdt2;
+        f3 xq = x;
+        if (has_plane) {
+            const float sd = dot(nn, xn) + plane.w - r;
+            if (sd < 0.0f) {
+                f3 v = sub(xn, x);
+                xn = sub(xn, scl(nn, sd));
+                const float vn = dot(v, nn);
+                if (vn < 0.0f) v = sub(v, scl(nn, -vn <= 2.0f * gdt2 ? vn : (1.0f + e) * vn));
+                xq = sub(xn, v);
+            }
+        }
+        xp = xq;
+        x = xn;
+    }
+    rec[0] = x.x;
+    rec[1] = x.y;
+    rec[2] = x.z;
+    pv[0] = xp.x;
+    pv[1] = xp.y;
+    pv[2] = xp.z;
 }
 
 // ============================================================ host helpers
@@ -676,11 +728,64 @@ rt_status rt_scene_free(rt_scene* s) {
     if (s->bvh_dev) cudaFree(s->bvh_dev);
     if (s->bvh_pinned) cudaFreeHost(s->bvh_pinned);
     if (s->bvh_copy_done) cudaEventDestroy(s->bvh_copy_done);
+    if (s->sky_dev) cudaFree(s->sky_dev);
     delete s;
     return RT_OK;
 }
 
 size_t rt_scene_bytes(const rt_scene* s) { return s ? s->bytes : 0; }
+
+rt_status rt_scene_set_sky(rt_scene* s, const float* texels, int32_t width, int32_t height, void* stream) {
+    if (!s) return RT_ERR_INVALID_ARG;
+    if (!texels) {
+        if (s->sky_dev) {
+            cudaDeviceSynchronize();  // renders in flight may still read it
+            cudaFree(s->sky_dev);
+        }
+        s->sky_dev = nullptr;
+        s->sky_w = s->sky_h = 0;
+        return RT_OK;
+    }
+    if (width < 1 || height < 1 || width > 16384 || height > 16384) return RT_ERR_INVALID_ARG;
+    const size_t n = (size_t)width * (size_t)height * 4;
+    if (!finite_all(texels, (int)n)) return RT_ERR_INVALID_ARG;  // n <= 2^30
+    if (s->sky_dev && (s->sky_w != width || s->sky_h != height)) {
+        cudaDeviceSynchronize();
+        cudaFree(s->sky_dev);
+        s->sky_dev = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!s->sky_dev) e = cudaMalloc(&s->sky_dev, n * 4);
+    // pageable source: the runtime stages it before returning
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sky_dev, texels, n * 4, cudaMemcpyHostToDevice,
+                                              static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_status(e);
+    s->sky_w = width;
+    s->sky_h = height;
+    return RT_OK;
+}
+
+rt_status rt_verlet_step(float* spheres_dev, float* prev_dev, int32_t n, const float* plane, float dt, float gravity,
+                         float restitution, int32_t steps, void* stream) {
+    if (n < 0 || steps < 0 || steps > (1 << 20) || (n && (!spheres_dev || !prev_dev)) ||
+        (reinterpret_cast<uintptr_t>(spheres_dev) & 3) || (reinterpret_cast<uintptr_t>(prev_dev) & 3))
+        return RT_ERR_INVALID_ARG;
+    if (!(dt > 0.0f) || !std::isfinite(dt) || !std::isfinite(gravity) || !(restitution >= 0.0f) ||
+        !(restitution <= 1.0f))
+        return RT_ERR_INVALID_ARG;
+    float4 pl = make_float4(0.f, 1.f, 0.f, 0.f);
+    if (plane) {
+        if (!finite_all(plane, 4)) return RT_ERR_INVALID_ARG;
+        const double nn = (double)plane[0] * plane[0] + (double)plane[1] * plane[1] + (double)plane[2] * plane[2];
+        if (std::fabs(nn - 1.0) > 1e-5) return RT_ERR_INVALID_ARG;
+        pl = make_float4(plane[0], plane[1], plane[2], plane[3]);
+    }
+    if (n == 0 || steps == 0) return RT_OK;
+    rt_verlet_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        spheres_dev, prev_dev, n, pl, plane ? 1 : 0, dt, gravity, restitution, steps);
+    g_launches++;
+    return cuda_status(cudaGetLastError());
+}
 
 size_t rt_hitrec_bytes(const rt_scene* s, const rt_render_params* p) {
     if (!s || !p || p->width < 1 || p->height < 1 || p->max_depth < 0) return 0;
@@ -897,7 +1002,7 @@ rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_r
     rt_status st = validate_params(s, p);
     if (st != RT_OK) return st;
     if ((st = validate_camera(cam)) != RT_OK) return st;
-    if (p->refl_coupled) return RT_ERR_UNSUPPORTED;
+    if (p->refl_coupled || s->sky_dev) return RT_ERR_UNSUPPORTED;
     if (!dl_dimg_dev || (reinterpret_cast<uintptr_t>(dl_dimg_dev) & 15) || dl_pitch_bytes < (size_t)p->width * 16 ||
         (dl_pitch_bytes & 15) || !grad_dev || (hitrec_dev && (reinterpret_cast<uintptr_t>(hitrec_dev) & 3)))
         return RT_ERR_INVALID_ARG;

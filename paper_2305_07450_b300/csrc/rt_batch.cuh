@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restr
     __shared__ const float4* s_geo;
     __shared__ const float4* s_mat;
     __shared__ const float4* s_mat2;
+    __shared__ SkyView s_sky;
     unsigned* counter = reinterpret_cast<unsigned*>(ws);
     const BatchFrame* frames = reinterpret_cast<const BatchFrame*>(ws + batch_frames_offset());
     const uint32_t* items = reinterpret_cast<const uint32_t*>(ws + batch_items_offset(n_frames));
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restr
                 s_geo = B->sv.geo;
                 s_mat = B->sv.mat;
                 s_mat2 = B->sv.mat2;
+                s_sky = B->sv.sky;
                 // shared memory was last read by the generic proxy; order those reads
                 // before the bulk copy's writes
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -87,8 +89,9 @@ __global__ void __launch_bounds__(128, 5) rt_batch_kernel(unsigned char* __restr
             cur = fi;
         }
         float4* tab = reinterpret_cast<float4*>(smem + sizeof(SceneHdr));
-        const StagedScene sc{reinterpret_cast<const SceneHdr*>(smem), CH ? nullptr : tab, s_geo,
-                             CH ? tab + (size_t)warp * kChunk : nullptr, s_mat, s_mat2};
+        StagedScene sc{reinterpret_cast<const SceneHdr*>(smem), CH ? nullptr : tab, s_geo,
+                       CH ? tab + (size_t)warp * kChunk : nullptr, s_mat, s_mat2};
+        sc.sky = s_sky;
         const int tx = tile % s_tiles_x, ty = tile / s_tiles_x;
         const int x = tx * block_x + (warp % wpr) * 8 + (lane & 7);
         const int y = ty * block_y + (warp / wpr) * 4 + (lane >> 3);

@@ -85,11 +85,19 @@ static_assert(sizeof(SceneHdr) % 16 == 0, "header must keep 16-byte alignment");
 // -r0^2, -r1^2).  Pad entries: centre 0, -r^2 = +1 (never hit, never block).
 // mat[i]  = (albedo r, g, b, k_s)
 // mat2[i] = (spec_exp, reflectivity, r, 1/r)
+// Sky panorama of the misses (Section 3.8): h rows of w RGBA texels from the top
+// row, or tex == nullptr (black).
+struct SkyView {
+    const float4* tex;
+    int w, h;
+};
+
 struct SceneView {
     const SceneHdr* hdr;
     const float4* geo;
     const float4* mat;
     const float4* mat2;
+    SkyView sky;
 };
 
 __host__ __device__ inline size_t scene_geo_offset() { return sizeof(SceneHdr); }

@@ -23,6 +23,7 @@ struct StagedScene {
     const float4* mat;     // global
     const float4* mat2;    // global
     BvhView bvh;           // hierarchy over the spheres (ACC kernels only)
+    SkyView sky;           // panorama of the misses (null: black)
 };
 
 // Tiled loop: entries [c0, c0 + m) of the global table into the warp's slot, copied
@@ -402,6 +403,29 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
     return out;
 }
 
+// ---------------------------------------------------------------- Section 3.8 sky
+// A ray that leaves the scene shows the sky panorama, looked up by the UV mapping
+// of its direction: u = 1/2 + atan2(d_z, d_x) / (2 pi), v = 1/2 - asin(d_y) / pi,
+// bilinear between texel centres, wrapping around in u, clamped to the first and
+// last rows in v.
+__device__ __forceinline__ float3 sky_lookup(const SkyView& sk, f3 d) {
+    const float dy = fminf(fmaxf(d.y, -1.0f), 1.0f);
+    const float u = fmaf(atan2f(d.z, d.x), 0.15915494309189535f, 0.5f);  // 1 / (2 pi)
+    const float v = fmaf(-asinf(dy), 0.31830988618379067f, 0.5f);        // 1 / pi
+    const float x = fmaf(u, (float)sk.w, -0.5f), y = fmaf(v, (float)sk.h, -0.5f);
+    const float x0 = floorf(x), y0 = floorf(y);
+    const float fx = x - x0, fy = y - y0;
+    int i0 = (int)x0;  // in [-1, w]: u in [0, 1]
+    i0 = i0 < 0 ? i0 + sk.w : (i0 >= sk.w ? i0 - sk.w : i0);
+    const int i1 = i0 + 1 == sk.w ? 0 : i0 + 1;
+    const int j0 = min(max((int)y0, 0), sk.h - 1), j1 = min(max((int)y0 + 1, 0), sk.h - 1);
+    const float4 a = __ldg(sk.tex + (size_t)j0 * sk.w + i0), b = __ldg(sk.tex + (size_t)j0 * sk.w + i1);
+    const float4 c = __ldg(sk.tex + (size_t)j1 * sk.w + i0), e = __ldg(sk.tex + (size_t)j1 * sk.w + i1);
+    const float tx = fmaf(fx, b.x - a.x, a.x), ty = fmaf(fx, b.y - a.y, a.y), tz = fmaf(fx, b.z - a.z, a.z);
+    const float bx = fmaf(fx, e.x - c.x, c.x), by = fmaf(fx, e.y - c.y, c.y), bz = fmaf(fx, e.z - c.z, c.z);
+    return make_float3(fmaf(fy, bx - tx, tx), fmaf(fy, by - ty, ty), fmaf(fy, bz - tz, tz));
+}
+
 // ---------------------------------------------------------------- hit geometry
 // Hit point and face-forwarded normal (sphere (p - c)/r, plane n; flipped to face
 // the incoming ray), computed once per hit with the ray origin as a hi + lo pair.
@@ -470,7 +494,7 @@ __device__ __forceinline__ f3 offset_origin(const HitGeom& hg, float eps, f3& lo
 // direction mirrored about n, v = -d), Blinn spec = max(n.h, 0)^exp.  The
 // reflection recursion of Section 3.7.1 is unrolled forward with a scalar
 // throughput: k < D adds T((1 - rho) A c + S) and sets T *= rho A; k = D adds
-// T(A c + S); a miss ends the path.  HITREC: write (id, t, vis_l) per bounce.
+// T(A c + S); a miss adds T sky(d) (nothing without a sky) and ends the path.  HITREC: write (id, t, vis_l) per bounce.
 template <bool HITREC, bool CH, bool ACC = false>
 __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame& fr, int x, int y,
                                               float* __restrict__ hr, size_t hr_plane, size_t hr_pix) {
@@ -490,7 +514,15 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
             rec[0] = __int_as_float(id);
             rec[hr_plane] = t;
         }
-        if (id < 0) break;
+        if (id < 0) {
+            if (sc.sky.tex) {  // a miss at bounce k adds T_k sky(d_k) (Section 3.8)
+                const float3 sk = sky_lookup(sc.sky, d);
+                out.x = fmaf(T, sk.x, out.x);
+                out.y = fmaf(T, sk.y, out.y);
+                out.z = fmaf(T, sk.z, out.z);
+            }
+            break;
+        }
         const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t, fr.refl_inv_max);
         f3 po_lo;
         const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);

@@ -111,6 +111,10 @@ def lib():
         L.rt_scene_build_bvh.restype = C.c_int
         L.rt_bvh_build_host.argtypes = [C.POINTER(SceneDesc), vp, i32, vp, C.POINTER(BvhInfo)]
         L.rt_bvh_build_host.restype = C.c_int
+        L.rt_scene_set_sky.argtypes = [vp, vp, i32, i32, vp]
+        L.rt_scene_set_sky.restype = C.c_int
+        L.rt_verlet_step.argtypes = [vp, vp, i32, vp, C.c_float, C.c_float, C.c_float, i32, vp]
+        L.rt_verlet_step.restype = C.c_int
         for name in ("rt_scene_upload", "rt_scene_update", "rt_scene_free", "rt_render",
                      "rt_device_errors", "rt_render_batch", "rt_batch_create", "rt_batch_launch",
                      "rt_batch_free"):
@@ -167,6 +171,18 @@ class DeviceScene:
         self.has_plane = scene.plane is not None
         self._keep = self._desc(scene)
         check("rt_scene_upload", lib().rt_scene_upload(C.byref(self._keep[0]), _stream(stream), C.byref(self._h)))
+        if getattr(scene, "sky", None) is not None:
+            self.set_sky(scene.sky, stream=stream)
+
+    def set_sky(self, texels, stream=None):
+        """rt_scene_set_sky: an [H, W, 4] FP32 panorama (host), or None for black misses."""
+        if texels is None:
+            check("rt_scene_set_sky", lib().rt_scene_set_sky(self._h, None, 0, 0, _stream(stream)))
+            return
+        t = np.ascontiguousarray(texels, dtype=np.float32)
+        assert t.ndim == 3 and t.shape[2] == 4
+        check("rt_scene_set_sky", lib().rt_scene_set_sky(self._h, t.ctypes.data, int(t.shape[1]), int(t.shape[0]),
+                                                         _stream(stream)))
 
     @staticmethod
     def _desc(scene: scenes.Scene):
@@ -227,6 +243,21 @@ class DeviceScene:
             self.close()
         except Exception:
             pass
+
+
+def verlet_step(spheres: torch.Tensor, prev: torch.Tensor, plane=None, *, dt: float = 1.0 / 60.0,
+                gravity: float = 9.81, restitution: float = 0.7, steps: int = 1, stream=None):
+    """rt_verlet_step: advance the device sphere records [N, 10] (centres in place)
+    and previous centres [N, 3] by `steps` Verlet steps; plane = record (nx, ny, nz,
+    d, ...) or None."""
+    for t in (spheres, prev):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    n = int(spheres.shape[0])
+    assert spheres.numel() == 10 * n and prev.numel() == 3 * n
+    pl = None if plane is None else np.ascontiguousarray(np.asarray(plane, np.float32)[:4])
+    check("rt_verlet_step", lib().rt_verlet_step(spheres.data_ptr(), prev.data_ptr(), n,
+                                                 pl.ctypes.data if pl is not None else None, float(dt), float(gravity),
+                                                 float(restitution), int(steps), _stream(stream)))
 
 
 NODE_DTYPE = np.dtype([("a_lo", "<f4", 3), ("a_hi", "<f4", 3), ("b_lo", "<f4", 3), ("b_hi", "<f4", 3),

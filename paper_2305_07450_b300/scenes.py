@@ -239,8 +239,8 @@ def sky_texture(seed: int = 7, width: int = 512, height: int = 256) -> np.ndarra
     3.8; the image itself is not available): float32 [height, width, 4], rows from
     the top (latitude +90 deg) down, columns over longitude.  A zenith-to-horizon
     blue gradient, a darker ground below the horizon, low-frequency cloud bands
-    (random harmonics in longitude and latitude) and one sun of HDR intensity 6 at
-    a random azimuth and elevation 20-60 deg; alpha 1."""
+    (random harmonics in longitude and latitude) and one soft sun of HDR intensity 4
+    (about 3.6 deg wide) at a random azimuth and elevation 20-60 deg; alpha 1."""
     rng = np.random.Generator(np.random.PCG64(seed))
     lat = (0.5 - (np.arange(height) + 0.5) / height) * np.pi          # +pi/2 .. -pi/2
     lon = ((np.arange(width) + 0.5) / width - 0.5) * 2.0 * np.pi       # -pi .. pi
@@ -259,7 +259,7 @@ def sky_texture(seed: int = 7, width: int = 512, height: int = 256) -> np.ndarra
     sun = np.array([np.cos(el) * np.cos(az), np.sin(el), np.cos(el) * np.sin(az)])
     dirs = np.stack([np.cos(LAT) * np.cos(LON), np.sin(LAT), np.cos(LAT) * np.sin(LON)], -1)
     cosang = np.clip(dirs @ sun, -1.0, 1.0)
-    col = col + 6.0 * np.exp(-(1.0 - cosang) / 2e-4)[..., None] * np.array([1.0, 0.95, 0.85])
+    col = col + 4.0 * np.exp(-(1.0 - cosang) / 2e-3)[..., None] * np.array([1.0, 0.95, 0.85])
     out = np.ones((height, width, 4), np.float32)
     out[..., :3] = col
     return f32(out)

@@ -79,7 +79,7 @@ MUTANTS = {
     "verlet_half_gravity": ("const double gdt2 = g * dt * dt;", "const double gdt2 = 0.5 * g * dt * dt;"),
     "verlet_restitution_ignored": ("(1.0 + e) * vn", "2.0 * vn"),
     "verlet_no_pushout": ("xn = sub(xn, scl(nn, sd));", ""),
-    "verlet_no_rest_contact": ("-vn <= gdt2 ? vn : (1.0 + e) * vn", "(1.0 + e) * vn"),
+    "verlet_no_rest_contact": ("-vn <= 2.0 * gdt2 ? vn : (1.0 + e) * vn", "(1.0 + e) * vn"),
     "verlet_prev_not_reset": ("xq = sub(xn, v);", "xq = x;"),
 }
 
