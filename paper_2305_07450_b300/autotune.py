@@ -150,3 +150,45 @@ def tune_batch(dscenes, scene_list, cameras, params_list, *, reps: int = 3, cand
              "candidates": {f"{a}x{b}": round(v, 4) for (a, b), v in results.items()}}
     _store(key, entry)
     return entry["launch"]
+
+
+def write_table(path: str, reps: int = 7) -> dict:
+    """Tune the standard workloads (forward at every workload, the 64-scene batch,
+    the animated loop's frames) with `reps` timed launches per candidate and write
+    the entries to `path`: the table shipped as tuned.json."""
+    global _mem
+    table = {}
+    stream = torch.cuda.current_stream()
+    names = ["256", "720p", "1080p", "4k", "4k_scene_1080p", "diff512"]
+    works = [scenes.WORKLOADS[n]() for n in names]
+    works += [scenes.paper_scene(W, H, s, d) for W, H in ((1280, 720), (1920, 1080), (3840, 2160))
+              for s, d in ((1, 1), (200, 3))]
+    works += [scenes.animated_scene(W, H)[0] for W, H in ((1280, 720), (1920, 1080), (3840, 2160))]
+    for w in works:
+        ds = rt.DeviceScene(w.scene)
+        tune_render(ds, w.scene, w.camera, w.params, reps=reps, stream=stream, force=True)
+        key = key_for(w.scene, w.params, "fwd")
+        table[key] = dict(_mem[key], workload=w.name)
+        ds.close()
+    ws = scenes.batch_scenes()
+    dss = [rt.DeviceScene(w.scene) for w in ws]
+    tune_batch(dss, [w.scene for w in ws], [w.camera for w in ws], [w.params for w in ws], reps=reps,
+               stream=stream, force=True)
+    for k, v in _mem.items():
+        if k.startswith("batch|"):
+            table[k] = dict(v, workload="64-scene batch")
+    for d in dss:
+        d.close()
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    return table
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="write the shipped launch table (run on the target GPU)")
+    ap.add_argument("--out", default=SHIPPED)
+    ap.add_argument("--reps", type=int, default=7)
+    a = ap.parse_args()
+    t = write_table(a.out, a.reps)
+    print(json.dumps({k: v["launch"] for k, v in t.items()}, indent=1))
