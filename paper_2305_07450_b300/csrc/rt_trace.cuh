@@ -487,14 +487,54 @@ __device__ __forceinline__ f3 offset_origin(const HitGeom& hg, float eps, f3& lo
     return hi;
 }
 
-// ---------------------------------------------------------------- Sections 3.5-3.7
-// Trace one pixel.  shade(c) = c A + S with
+// ---------------------------------------------------------------- Sections 3.5-3.8
+// A miss at bounce k adds T_k sky(d_k) (Section 3.8); nothing without a sky.
+__device__ __forceinline__ void miss_add(const StagedScene& sc, f3 d, float T, float3& out) {
+    if (sc.sky.tex) {
+        const float3 sk = sky_lookup(sc.sky, d);
+        out.x = fmaf(T, sk.x, out.x);
+        out.y = fmaf(T, sk.y, out.y);
+        out.z = fmaf(T, sk.z, out.z);
+    }
+}
+
+// The hit of bounce k: primitive id at distance t of the ray (o + o_lo, d) that
+// carries throughput T.  shade(c) = c A + S with
 //   A = k_a + sum_l I_l vis_l max(n.l, 0),  S = sum_l I_l vis_l k_s spec_l,
 // a light skipped when n.l <= 0; Phong spec = max(v.r, 0)^exp (r the light
 // direction mirrored about n, v = -d), Blinn spec = max(n.h, 0)^exp.  The
-// reflection recursion of Section 3.7.1 is unrolled forward with a scalar
-// throughput: k < D adds T((1 - rho) A c + S) and sets T *= rho A; k = D adds
-// T(A c + S); a miss adds T sky(d) (nothing without a sky) and ends the path.  HITREC: write (id, t, vis_l) per bounce.
+// reflection recursion of Section 3.7.1 unrolled forward: below the depth limit it
+// adds T((1 - rho) A c + S) and turns (o, o_lo, d, T) into the reflected ray with
+// T *= rho A; at the limit it adds T(A c + S).  HITREC: vis_l at hr[hr_k + ...].
+template <bool HITREC, bool CH, bool ACC>
+__device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, int id,
+                                           float t, f3& o, f3& o_lo, f3& d, float& T, float3& out,
+                                           float* __restrict__ hr, size_t hr_k, size_t hr_plane) {
+    const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t, fr.refl_inv_max);
+    f3 po_lo;
+    const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);
+    const float4 m = hg.m, m2 = hg.m2;
+    const HitShade sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+    const float A = sh.A, S = sh.S;
+    if (k < fr.D) {
+        const float w = T * (1.0f - m2.y) * A;
+        out.x = fmaf(w, m.x, fmaf(T, S, out.x));
+        out.y = fmaf(w, m.y, fmaf(T, S, out.y));
+        out.z = fmaf(w, m.z, fmaf(T, S, out.z));
+        T *= m2.y * A;
+        d = normalize_rn(fma3(n, -2.0f * dot(d, n), d));
+        o = po;
+        o_lo = po_lo;
+    } else {
+        const float w = T * A;
+        out.x = fmaf(w, m.x, fmaf(T, S, out.x));
+        out.y = fmaf(w, m.y, fmaf(T, S, out.y));
+        out.z = fmaf(w, m.z, fmaf(T, S, out.z));
+    }
+}
+
+// Trace one pixel: bounce by bounce, closest hit (Section 3.4.1), then miss_add or
+// shade_step.  HITREC: write (id, t, vis_l) per bounce, id = -1 after the path ends.
 template <bool HITREC, bool CH, bool ACC = false>
 __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame& fr, int x, int y,
                                               float* __restrict__ hr, size_t hr_plane, size_t hr_pix) {
@@ -515,36 +555,11 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
             rec[hr_plane] = t;
         }
         if (id < 0) {
-            if (sc.sky.tex) {  // a miss at bounce k adds T_k sky(d_k) (Section 3.8)
-                const float3 sk = sky_lookup(sc.sky, d);
-                out.x = fmaf(T, sk.x, out.x);
-                out.y = fmaf(T, sk.y, out.y);
-                out.z = fmaf(T, sk.z, out.z);
-            }
+            miss_add(sc, d, T, out);
             break;
         }
-        const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t, fr.refl_inv_max);
-        f3 po_lo;
-        const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);
-        const float4 m = hg.m, m2 = hg.m2;
-        const size_t hr_k = (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
-        const HitShade sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
-        const float A = sh.A, S = sh.S;
-        if (k < fr.D) {
-            const float w = T * (1.0f - m2.y) * A;
-            out.x = fmaf(w, m.x, fmaf(T, S, out.x));
-            out.y = fmaf(w, m.y, fmaf(T, S, out.y));
-            out.z = fmaf(w, m.z, fmaf(T, S, out.z));
-            T *= m2.y * A;
-            d = normalize_rn(fma3(n, -2.0f * dot(d, n), d));
-            o = po;
-            o_lo = po_lo;
-        } else {
-            const float w = T * A;
-            out.x = fmaf(w, m.x, fmaf(T, S, out.x));
-            out.y = fmaf(w, m.y, fmaf(T, S, out.y));
-            out.z = fmaf(w, m.z, fmaf(T, S, out.z));
-        }
+        shade_step<HITREC, CH, ACC>(sc, fr, pix, k, id, t, o, o_lo, d, T, out, hr,
+                                    (size_t)k * (2 + h.nl) * hr_plane + hr_pix, hr_plane);
     }
     if (HITREC) {
         for (int kk = k + 1; kk <= fr.D; ++kk)
@@ -565,17 +580,13 @@ __device__ __forceinline__ uint32_t pack_rgba8(float3 c) {
     return quant8(c.x) | (quant8(c.y) << 8) | (quant8(c.z) << 16) | 0xFF000000u;
 }
 
-// Trace pixel (x, y) of the frame and store it at (x - rx0, y - ry0) of `out`.  All
+// Store the colour of pixel (x, y) of the frame at (x - rx0, y - ry0) of `out`.  All
 // 32 lanes of the warp must call (the RGBA8 path gathers four horizontally adjacent
 // pixels, lanes 4j..4j+3, into one 16-byte store; rx0 is a multiple of 8); `valid`
 // marks lanes whose pixel is inside the rendered region.
-template <bool HITREC, bool CH, bool ACC = false>
-__device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
-                                             void* __restrict__ out, size_t pitch, float* __restrict__ hr,
-                                             size_t hr_plane) {
+__device__ __forceinline__ void store_pixel(const Frame& fr, int x, int y, bool valid, float3 c,
+                                            void* __restrict__ out, size_t pitch) {
     const int lane = threadIdx.x & 31;
-    float3 c = make_float3(0.f, 0.f, 0.f);
-    if (valid) c = trace_pixel<HITREC, CH, ACC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
     const int lx = x - fr.rx0, ly = y - fr.ry0;
     if (fr.fmt == RT_OUT_F32) {
         if (valid)
@@ -597,6 +608,16 @@ __device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame&
             }
         }
     }
+}
+
+// Trace pixel (x, y) of the frame and store it (store_pixel's rules).
+template <bool HITREC, bool CH, bool ACC = false>
+__device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
+                                             void* __restrict__ out, size_t pitch, float* __restrict__ hr,
+                                             size_t hr_plane) {
+    float3 c = make_float3(0.f, 0.f, 0.f);
+    if (valid) c = trace_pixel<HITREC, CH, ACC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
+    store_pixel(fr, x, y, valid, c, out, pitch);
 }
 
 }  // namespace rtd
