@@ -225,3 +225,54 @@ def test_paper_scene_soft_shadows(samples, depth):
     at bounce 1, and 200 sunflower samples at bounce 3 (Sections 3.6.1, 4)."""
     w = S.paper_scene(128, 72, samples, depth)
     check_f32_full(w, min_plain=0.995)
+
+
+def test_maximum_lights_samples_and_depth():
+    """The ABI's maxima at once: 16 lights (point, square-area and spherical), 1024
+    shadow samples per sampled light, bounce limit 16 -- two large mirror spheres
+    facing each other along the view axis send the central ray through all 16
+    reflections; every pixel against the oracle."""
+    rng = np.random.default_rng(16)
+    sph = [sphere((0.0, 1.0, 6.0), 3.0, albedo=(0.2, 0.3, 0.9), refl=0.95),
+           sphere((0.0, 1.0, -6.0), 3.0, albedo=(0.9, 0.3, 0.2), refl=0.95),
+           sphere((-1.2, 0.6, 1.5), 0.5, albedo=(0.3, 0.9, 0.3), refl=0.5),
+           sphere((1.3, 1.8, 1.0), 0.4, albedo=(0.9, 0.9, 0.2), refl=0.5),
+           sphere((0.8, 0.4, -1.4), 0.35, albedo=(0.8, 0.2, 0.8), refl=0.5)]
+    lig = [light((float(rng.uniform(-6, 6)), float(rng.uniform(8, 10)), float(rng.uniform(-3, 3))),
+                 float(rng.uniform(0.05, 0.1))) for _ in range(12)]
+    lig += [light((-2.0, 9.5, -1.0), 0.2, area=1.0), light((2.5, 9.0, 1.5), 0.2, area=0.7)]
+    lig += [light((0.0, 10.0, 0.5), 0.2, srad=0.4), light((-3.0, 9.0, 2.0), 0.2, srad=0.3)]
+    assert len(lig) == 16
+    sc, cam, p = mk(spheres=sph, plane=plane_rec(refl=0.6), lights=lig, camera=(0, 1, 0, 0, 0, 50),
+                    W=20, H=14, D=16, samples=1024, seed=99)
+    p.eps = 5e-4
+    w = as_workload("max_lights_samples_depth", sc, cam, p)
+    check_f32_full(w, min_plain=0.97)
+    img, hr = gpu_render(w, hitrec=True)
+    rec = hr.reshape(p.max_depth + 1, 2 + 16, p.height, p.width)
+    assert rec[16, 0, 7, 10].view(np.int32) >= 0        # the axial ray is still hitting at bounce 16
+
+
+def test_maximum_frame_dimensions():
+    """Frames at the ABI's 32768-pixel limit: a 32768 x 8 strip (every pixel
+    rendered, sampled parity) and 64 x 4 regions at the corners of a 32768 x 32768
+    frame (the NDC of the full frame), against the oracle."""
+    w = S.whitted_256()
+    w.params.width, w.params.height = 32768, 8
+    img, _ = gpu_render(w, fmt=S.OUT_F32)
+    px = S.pixel_lattice(w.params.width, w.params.height, 997, seed=5, n_random=200)
+    ref, margin, sens = oracle_reference(w, px)
+    ok, st = compare_f32(img[px[:, 1], px[:, 0], :3], ref, margin, sens, w.scene.scene_scale)
+    assert st["failing"] == 0, st
+    w = S.whitted_256()
+    w.params.width = w.params.height = 32768
+    w.params.out_format = S.OUT_F32
+    ds = rt.DeviceScene(w.scene)
+    for x0, y0 in ((0, 0), (32768 - 64, 32768 - 4), (16384, 16382)):
+        sub = rt.render_region(ds, w.camera, w.params, x0, y0, 64, 4).cpu().numpy()
+        xs, ys = np.meshgrid(np.arange(x0, x0 + 64), np.arange(y0, y0 + 4))
+        px = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+        ref, margin, sens = oracle_reference(w, px)
+        ok, st = compare_f32(sub[..., :3].reshape(-1, 3), ref, margin, sens, w.scene.scene_scale)
+        assert st["failing"] == 0, (x0, y0, st)
+    ds.close()
