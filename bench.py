@@ -183,6 +183,15 @@ def recorded_traffic(workload_name: str):
     return None
 
 
+def workload_config(w: S.Workload, world: int) -> dict:
+    """The `config` object of both arms' JSON lines: what the workload is."""
+    return {"workload": w.name, "width": w.params.width, "height": w.params.height, "spheres": w.scene.n_spheres,
+            "lights": w.scene.n_lights, "max_depth": w.params.max_depth,
+            "shadow_samples": w.params.shadow_samples, "out": "rgba8" if w.params.out_format == 0 else "f32",
+            "l2": f"flushed between timed frames ({L2_FLUSH_BYTES >> 20} MB write)",
+            "parallelism": f"replicas x{world}"}
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -272,11 +281,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic: seeded scene (PCG64), no dataset",
-            "config": {"workload": w.name, "width": W, "height": H, "spheres": w.scene.n_spheres,
-                       "lights": w.scene.n_lights, "max_depth": w.params.max_depth,
-                       "shadow_samples": w.params.shadow_samples, "out": "rgba8" if w.params.out_format == 0 else "f32",
-                       "l2": f"flushed between timed frames ({L2_FLUSH_BYTES >> 20} MB write)",
-                       "parallelism": f"replicas x{world}", "launch": dict(launch, chosen_by="autotune")},
+            "config": dict(workload_config(w, world), launch=dict(launch, chosen_by="autotune")),
             "clocks": clocks,
             "gpu_launches": int(launches),
         }
@@ -523,7 +528,7 @@ def run_reference(args):
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 / fps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic: seeded scene (PCG64), no dataset",
-        "config": {"workload": w.name},
+        "config": workload_config(w, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": info["threads"], "kind": "oracle",
                          "sample": f"{info['pixels']} pixels (lattice stride {info['stride']}) per step, "
                                    f"scaled to frames/s", "cpu": host_cpu_name()},
