@@ -159,12 +159,16 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- traffic record
+# the sources the forward kernel is compiled from (its translation unit and the
+# headers it includes); the batch and adjoint kernels' headers do not change it
+FWD_SOURCES = ("rt_api.cu", "rt_device.cuh", "rt_trace.cuh", "rt_stage.cuh", "rt_bvh.cuh", "rt_errword.cuh")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_07450_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in FWD_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
