@@ -7,12 +7,15 @@
 //
 // Why nothing is culled.  Boxes hold their spheres' exact extents (rounded outward
 // on the host).  A sphere the FP32 test accepts at parameter t has its point o + t d
-// within r + 26u M of the centre (u = 2^-24, M = |o|_inf + R, R the largest
-// |c|_inf + r of the scene), and the FP32 slab parameters are within 5u M / |d_axis|
-// of the exact ones (d the ray direction, or the vector V of a shadow segment
-// o + u V, u in [0, 1]).  Every box is therefore widened, per ray, by
-// delta = 2^-16 M = 256u M per side, eight times what the two bounds need; the box
-// then starts before t and ends after it, in FP32 too.
+// within r + 31u M of the centre (u = 2^-24, M = |o|_inf + R, R the largest
+// |c|_inf + r of the scene: each component of c x d - o x d is off by at most 7u M,
+// so the line passes within r + 17u M of the centre, and tca = c.d - o.d with the
+// root's rounding moves t by at most 14u M along d), and the FP32 slab parameters
+// are within 5u M / |d_axis| of the exact ones (d the ray direction, or the vector
+// V of a shadow segment o + u V, u in [0, 1]; the segment test's point is within
+// r + 26u M).  Every box is therefore widened, per ray, by delta = 2^-16 M = 256u M
+// per side, seven times what the two bounds need; the box then starts before t
+// and ends after it, in FP32 too.
 #pragma once
 
 #include "rt_device.cuh"
@@ -51,16 +54,29 @@ __host__ __device__ inline size_t bvh_bytes(int n_nodes, int ns) {
 // ---------------------------------------------------------------- per sphere
 // The brute-force block tests of Sections 3.4.1 and 3.6 for one sphere g = (c, -r^2),
 // element for element the operations of the packed pair tests, in the same order
-// (closest root; blocked segment o + u V, u = clamp(oc.W, 0, 1), -V = nv).
-__device__ __forceinline__ bool sphere_root_t(float4 g, f3 o, f3 d, float& t) {
-    const float ocx = g.x + (-o.x), ocy = g.y + (-o.y), ocz = g.z + (-o.z);
-    const float tca = fmaf(ocx, d.x, fmaf(ocy, d.y, ocz * d.z));
-    const float lx = fmaf(tca, -d.x, ocx), ly = fmaf(tca, -d.y, ocy), lz = fmaf(tca, -d.z, ocz);
-    const float m = fmaf(lx, lx, fmaf(ly, ly, fmaf(lz, lz, g.w)));
+// (closest root from m = |c x d - o x d|^2 - r^2 and tca = c.d - o.d; blocked
+// segment o + u V, u = clamp(oc.W, 0, 1), -V = nv).
+struct RayX {  // -(o x d) and -(o.d) of a ray, formed once per ray
+    f3 nw;
+    float nod;
+};
+__device__ __forceinline__ RayX ray_x(f3 o, f3 d) {
+    RayX x;
+    x.nw = mk3(fmaf(o.z, d.y, -(o.y * d.z)), fmaf(o.x, d.z, -(o.z * d.x)), fmaf(o.y, d.x, -(o.x * d.y)));
+    x.nod = -dot(o, d);
+    return x;
+}
+
+__device__ __forceinline__ bool sphere_root_t(float4 g, const RayX& x, f3 d, float& t) {
+    const float px = fmaf(g.y, d.z, fmaf(g.z, -d.y, x.nw.x));
+    const float py = fmaf(g.z, d.x, fmaf(g.x, -d.z, x.nw.y));
+    const float pz = fmaf(g.x, d.y, fmaf(g.y, -d.x, x.nw.z));
+    const float m = fmaf(px, px, fmaf(py, py, fmaf(pz, pz, g.w)));
     if (!(m < 0.0f)) return false;
+    const float tc = fmaf(g.x, d.x, fmaf(g.y, d.y, fmaf(g.z, d.z, x.nod)));
     const float s = __fsqrt_rn(-m);
-    t = tca - s;
-    if (t <= 0.0f) t = tca + s;
+    t = tc - s;
+    if (t <= 0.0f) t = tc + s;
     return t > 0.0f;
 }
 
@@ -133,6 +149,7 @@ __device__ __noinline__ void closest_bvh(const float4* __restrict__ geo, const B
                                             int& best) {
     if (bv.n_nodes <= 0) return;
     const RayInv q = ray_inv(o, d, bv.r_scene);
+    const RayX rx = ray_x(o, d);
     int stack[kBvhStack];
     float stack_t[kBvhStack];
     int sp = 0;
@@ -173,7 +190,7 @@ __device__ __noinline__ void closest_bvh(const float4* __restrict__ geo, const B
             for (int k = 0; k < cnt; ++k) {
                 const int i = bv.prim[first + k];
                 float t;
-                if (sphere_root_t(sphere_at(geo, i), o, d, t) && (t < tb || (t == tb && i < best))) {
+                if (sphere_root_t(sphere_at(geo, i), rx, d, t) && (t < tb || (t == tb && i < best))) {
                     tb = t;
                     best = i;
                 }

@@ -53,36 +53,46 @@ __device__ __forceinline__ f3 primary_dir(const Frame& fr, int x, int y) {
 
 // ---------------------------------------------------------------- Section 3.4.1
 // Closest of all primitives by brute force; spheres 0..N-1 then the plane N; a
-// strictly smaller distance wins, so ties keep the lower index.  Sphere test in the
-// well-conditioned form: with oc = c - o and tca = oc.d, the squared distance of
-// the centre from the ray's line is |oc - tca d|^2, so m = |oc - tca d|^2 - r^2
-// (the negated discriminant) avoids the cancellation of tca^2 - |oc|^2 for distant
-// spheres; a hit needs m < 0, at tca -+ sqrt(-m): the near root if it is > 0, else
-// the far one.  The two spheres of a pair are tested by the same packed
-// instructions; a block of kPad spheres computes its m branch-free and takes the
-// roots only when one of them is negative (one branch per block).
-struct RayPair {  // -o, d and -d in both halves of a pair
-    float2 nox, noy, noz, dx, dy, dz, ndx, ndy, ndz;
+// strictly smaller distance wins, so ties keep the lower index.  Sphere test: the
+// vector from the ray's line to the centre has length |(c - o) x d| (d is a unit
+// vector), so m = |c x d - o x d|^2 - r^2 is the negated discriminant; with
+// -(o x d) formed once per ray, a pair of spheres costs three packed FMAs per
+// component and three for the square (9 packed instructions; the projection form
+// oc - (oc.d) d needs 12).  Both forms round the same long terms (|c|, |o| of tens
+// of units) once each and neither subtracts squares of them, so m keeps an
+// absolute error of a few ulps of those terms.  A hit needs m < 0; its distance
+// tca -+ sqrt(-m), tca = c.d - o.d, is formed only for those spheres: the near
+// root if it is > 0, else the far one.  The two spheres of a pair are tested by
+// the same packed instructions; a block of kPad spheres computes its m branch-free
+// and takes the roots only when one of them is negative (one branch per block).
+struct RayPair {  // -o in both halves of a pair (shadow segments)
+    float2 nox, noy, noz;
 };
-__device__ __forceinline__ RayPair ray_pair(f3 o, f3 d) {
-    return RayPair{dup2(-o.x), dup2(-o.y), dup2(-o.z), dup2(d.x), dup2(d.y),
-                   dup2(d.z),  dup2(-d.x), dup2(-d.y), dup2(-d.z)};
+__device__ __forceinline__ RayPair ray_pair(f3 o) { return RayPair{dup2(-o.x), dup2(-o.y), dup2(-o.z)}; }
+
+struct RayCross {  // d, -d and -(o x d) in both halves of a pair; -(o.d)
+    float2 dx, dy, dz, ndx, ndy, ndz, nwx, nwy, nwz;
+    float nod;
+};
+__device__ __forceinline__ RayCross ray_cross(f3 o, f3 d) {
+    const RayX x = ray_x(o, d);
+    return RayCross{dup2(d.x),    dup2(d.y),    dup2(d.z),    dup2(-d.x), dup2(-d.y),
+                    dup2(-d.z),   dup2(x.nw.x), dup2(x.nw.y), dup2(x.nw.z), x.nod};
 }
 
 // One block of kPad spheres (kPad / 2 pairs at geo[0..kPad)); base = index of its first sphere.
-__device__ __forceinline__ void closest_block(const float4* __restrict__ geo, int base, const RayPair& r, float& tb,
+__device__ __forceinline__ void closest_block(const float4* __restrict__ geo, int base, const RayCross& r, float& tb,
                                               int& best) {
-    float2 tca[kPad / 2], m[kPad / 2];
+    float2 m[kPad / 2];
     uint32_t neg = 0;
 #pragma unroll
     for (int q = 0; q < kPad / 2; ++q) {
         const float4 A = geo[2 * q], B = geo[2 * q + 1];
-        const float2 ocx = add2(make_float2(A.x, A.y), r.nox);
-        const float2 ocy = add2(make_float2(A.z, A.w), r.noy);
-        const float2 ocz = add2(make_float2(B.x, B.y), r.noz);
-        tca[q] = fma2(ocx, r.dx, fma2(ocy, r.dy, mul2(ocz, r.dz)));
-        const float2 lx = fma2(tca[q], r.ndx, ocx), ly = fma2(tca[q], r.ndy, ocy), lz = fma2(tca[q], r.ndz, ocz);
-        m[q] = fma2(lx, lx, fma2(ly, ly, fma2(lz, lz, make_float2(B.z, B.w))));
+        const float2 cx = make_float2(A.x, A.y), cy = make_float2(A.z, A.w), cz = make_float2(B.x, B.y);
+        const float2 px = fma2(cy, r.dz, fma2(cz, r.ndy, r.nwx));
+        const float2 py = fma2(cz, r.dx, fma2(cx, r.ndz, r.nwy));
+        const float2 pz = fma2(cx, r.dy, fma2(cy, r.ndx, r.nwz));
+        m[q] = fma2(px, px, fma2(py, py, fma2(pz, pz, make_float2(B.z, B.w))));
         neg |= __float_as_uint(m[q].x) | __float_as_uint(m[q].y);
     }
     if (neg >> 31) {
@@ -92,7 +102,9 @@ __device__ __forceinline__ void closest_block(const float4* __restrict__ geo, in
             for (int hf = 0; hf < 2; ++hf) {
                 const float mm = hf ? m[q].y : m[q].x;
                 if (mm < 0.0f) {
-                    const float tc = hf ? tca[q].y : tca[q].x;
+                    const float4 A = geo[2 * q], B = geo[2 * q + 1];
+                    const float cx = hf ? A.y : A.x, cy = hf ? A.w : A.z, cz = hf ? B.y : B.x;
+                    const float tc = fmaf(cx, r.dx.x, fmaf(cy, r.dy.x, fmaf(cz, r.dz.x, r.nod)));
                     const float s = __fsqrt_rn(-mm);
                     float t = tc - s;
                     if (t <= 0.0f) t = tc + s;
@@ -114,7 +126,7 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
     if constexpr (ACC) {
         closest_bvh(sc.geo, sc.bvh, o, d, tb, best);
     } else {
-        const RayPair rp = ray_pair(o, d);
+        const RayCross rp = ray_cross(o, d);
         if constexpr (CH) {
             const unsigned mask = __activemask();
 #pragma unroll 1
@@ -222,7 +234,7 @@ __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, cons
             if (!occ[r]) occ[r] = occluded_bvh(sc.geo, sc.bvh, o, w[r], nv[r]);
     } else {
         const unsigned mask = __activemask();
-        const RayPair o2 = ray_pair(o, mk3(0.f, 0.f, 0.f));
+        const RayPair o2 = ray_pair(o);
         SegPair sg[kShadowGroup];
         uint32_t acc[kShadowGroup];
 #pragma unroll
