@@ -231,6 +231,34 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *cam, const rt_render
                     void *out_dev, size_t out_pitch_bytes, void *hitrec_dev,
                     const rt_launch_config *cfg, void *stream);
 
+/* Device workspace bytes rt_render_ws suggests for this frame (256-byte aligned
+ * buffer): a 256-byte control block and two path queues of ceil(W*H/4) entries of
+ * 64 bytes each (about 133 bytes per 4 pixels; 265 MB at 3840x2160).  0 on
+ * invalid arguments. */
+size_t rt_render_workspace_bytes(const rt_scene *scene, const rt_render_params *params);
+
+/* Render one frame as rt_render does -- the same arguments, and every pixel and
+ * hit-record entry bit for bit the same -- in passes over compacted paths, using
+ * the caller's workspace (no allocation).  A warp of the one-pass kernel runs the
+ * bounce loop until its slowest lane is done, so a few pixels whose reflections
+ * keep hitting idle the rest of their warp; here persistent warps trace every
+ * pixel's primary ray, its shading and its bounce-1 ray, and hand the paths whose
+ * bounce-1 ray hits to a queue; pass k (k = 1..D) then shades the queued bounce-k
+ * hits 32 per warp and queues those whose next ray hits again.  Not in the paper
+ * (an execution strategy of its Section 3.7 recursion).
+ *   workspace_dev, workspace_bytes: a device buffer, 256-byte aligned, of at least
+ *            256 bytes; queue capacity = (workspace_bytes - 256) / 128 paths.  A
+ *            smaller workspace is correct: paths that find their queue full are
+ *            finished by the lane that holds them.
+ * Enqueued on `stream`: one 256-byte memset, then D + 1 kernel launches (a pass
+ * whose queue is empty returns at once).  The workspace must not be reused by
+ * another call before this one completes (stream order or events).  The staged
+ * brute-force path uses the queues; the hierarchy (cfg->accel = 1) and scenes too
+ * large for shared memory render exactly as rt_render (the workspace unused). */
+rt_status rt_render_ws(const rt_scene *scene, const rt_camera *cam, const rt_render_params *params,
+                       void *out_dev, size_t out_pitch_bytes, void *hitrec_dev, const rt_launch_config *cfg,
+                       void *workspace_dev, size_t workspace_bytes, void *stream);
+
 /* ---------------------------------------------------------------- batches
  * Many frames (scenes of uneven sphere counts and resolutions) rendered by ONE
  * persistent kernel launch: the (frame, tile) work items are ordered longest

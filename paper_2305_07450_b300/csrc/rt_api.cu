@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "../../include/rt.h"
@@ -93,6 +94,101 @@ __global__ void __maxnreg__(80) rt_fwd_kernel(const SceneView sv, const Frame fr
     const int y = fr.ry0 + blockIdx.y * block_y + (warp / wpr) * 4 + (lane >> 3);
     const bool valid = x < fr.rx1 && y < fr.ry1;
     render_pixel<HITREC, CH>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
+}
+
+// ============================================================ queued render (rt_render_ws)
+// Workspace: a control block of counters, then two path queues of `cap` entries
+// (64 bytes each) used in turn: queue k (the paths whose bounce-k ray hit) lives in
+// the first when k is odd, in the second when k is even.
+struct WsCtl {
+    unsigned claim0;                    // warp patches claimed by the first pass
+    unsigned count[RT_MAX_DEPTH + 2];   // entries appended to queue k
+    unsigned head[RT_MAX_DEPTH + 2];    // entries claimed from queue k
+};
+constexpr size_t kWsCtlBytes = 256;
+constexpr size_t kWsEntryBytes = 64;
+static_assert(sizeof(WsCtl) <= kWsCtlBytes, "workspace control block");
+
+__host__ __device__ inline unsigned ws_cap(size_t bytes) {
+    return bytes <= kWsCtlBytes ? 0u : (unsigned)std::min<size_t>((bytes - kWsCtlBytes) / (2 * kWsEntryBytes), 1u << 30);
+}
+__device__ __forceinline__ PathQueue ws_queue(unsigned char* ws, unsigned cap, int k) {
+    WsCtl* c = reinterpret_cast<WsCtl*>(ws);
+    float4* q = reinterpret_cast<float4*>(ws + kWsCtlBytes + ((k & 1) ? 0 : (size_t)cap * kWsEntryBytes));
+    return PathQueue{q, &c->count[k], cap};
+}
+
+// First pass: persistent CTAs (one per resident slot) stage the scene once; each
+// warp claims 8 x 4 pixel patches (in the order of block_x x block_y tiles) and
+// traces them, pushing paths whose bounce-1 ray hits to queue 1.
+template <bool HITREC>
+__global__ void __maxnreg__(80) rt_fwd_p0_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
+                                                 size_t pitch, float* __restrict__ hr, size_t hr_plane, int staging,
+                                                 int block_x, int block_y, int tiles_x, unsigned n_items,
+                                                 unsigned char* __restrict__ ws, unsigned cap) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (staging == 1 && tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const uint32_t stage_bytes = (uint32_t)(sizeof(SceneHdr) + 16u * (uint32_t)__ldg(&sv.hdr->ns_pad));
+    if (!stage_to_smem(smem, sv.hdr, stage_bytes, staging, &bar, phase, &g_err_word)) return;
+    const int lane = threadIdx.x;
+    const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
+    StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
+    sc.sky = sv.sky;
+    WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
+    const PathQueue q1 = ws_queue(ws, cap, 1);
+    const int wpr = block_x >> 3, wpt = (block_x * block_y) >> 5;
+#pragma unroll 1
+    while (true) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(&ctl->claim0, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const int tile = (int)(it / (unsigned)wpt), wi = (int)(it % (unsigned)wpt);
+        const int x = fr.rx0 + (tile % tiles_x) * block_x + (wi % wpr) * 8 + (lane & 7);
+        const int y = fr.ry0 + (tile / tiles_x) * block_y + (wi / wpr) * 4 + (lane >> 3);
+        const bool valid = x < fr.rx1 && y < fr.ry1;
+        render_pixel<HITREC, false>(sc, fr, x, y, valid, out, pitch, hr, hr_plane, fr.D >= 1 ? &q1 : nullptr);
+    }
+}
+
+// Pass k >= 1: persistent CTAs; each warp claims 32 entries of queue k at a time.
+// CTAs beyond the ones the queue's length needs return before staging.
+template <bool HITREC>
+__global__ void __maxnreg__(80) rt_fwd_queue_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
+                                                    size_t pitch, float* __restrict__ hr, size_t hr_plane,
+                                                    int staging, unsigned char* __restrict__ ws, unsigned cap, int k) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
+    const unsigned n = min(*reinterpret_cast<volatile unsigned*>(&ctl->count[k]), cap);
+    const unsigned per_cta = 32u * blockDim.y;
+    if ((unsigned)blockIdx.x * per_cta >= n) return;  // the whole CTA, before any barrier
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (staging == 1 && tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const uint32_t stage_bytes = (uint32_t)(sizeof(SceneHdr) + 16u * (uint32_t)__ldg(&sv.hdr->ns_pad));
+    if (!stage_to_smem(smem, sv.hdr, stage_bytes, staging, &bar, phase, &g_err_word)) return;
+    const int lane = threadIdx.x;
+    const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
+    StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
+    sc.sky = sv.sky;
+    const PathQueue cur = ws_queue(ws, cap, k);
+    const PathQueue nxt = ws_queue(ws, cap, k + 1);
+#pragma unroll 1
+    while (true) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->head[k], 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        const unsigned i = base + (unsigned)lane;
+        if (i < n) trace_queued<HITREC>(sc, fr, cur.ent + (size_t)i * 4, k, nxt, out, pitch, hr, hr_plane);
+        __syncwarp();
+    }
 }
 
 // Forward kernel over the sphere hierarchy: the same pixels as rt_fwd_kernel, the
@@ -428,6 +524,27 @@ size_t stage_smem_bytes(bool chunked, int ns_pad, int nwarps) {
 bool use_tiled_loop(const Launch& L, int ns_pad) {
     if (L.staging == 3) return true;
     return stage_smem_bytes(false, ns_pad, 0) + 4096 > (size_t)(max_smem_optin() - 1024);
+}
+
+// Resident CTAs of `kernel` on the current device (threads per CTA, dynamic shared
+// memory), cached per (device, kernel, threads, bytes).
+template <typename K>
+int resident_ctas(K kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::vector<std::tuple<int, const void*, int, size_t, int>> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto& e : cache)
+        if (std::get<0>(e) == dev && std::get<1>(e) == (const void*)kernel && std::get<2>(e) == threads &&
+            std::get<3>(e) == smem)
+            return std::get<4>(e);
+    int per_sm = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) per_sm = 1;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 1;
+    const int n = std::max(1, per_sm) * std::max(1, nsm);
+    cache.emplace_back(dev, (const void*)kernel, threads, smem, n);
+    return n;
 }
 
 template <typename K>
@@ -794,7 +911,8 @@ size_t rt_hitrec_bytes(const rt_scene* s, const rt_render_params* p) {
 
 static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt_render_params* p, int32_t x0,
                                int32_t y0, int32_t rw, int32_t rh, void* out_dev, size_t out_pitch_bytes,
-                               void* hitrec_dev, const rt_launch_config* cfg, void* stream) {
+                               void* hitrec_dev, const rt_launch_config* cfg, void* stream, void* ws = nullptr,
+                               size_t ws_bytes = 0) {
     rt_status st = validate_params(s, p);
     if (st != RT_OK) return st;
     if ((st = validate_camera(cam)) != RT_OK) return st;
@@ -848,6 +966,35 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
     }
     const bool chunked = use_tiled_loop(L, s->ns_pad);
     const size_t smem = stage_smem_bytes(chunked, s->ns_pad, nwarps);
+    if (ws && !chunked) {
+        // queued render: reset the counters, first pass, then one pass per bounce
+        unsigned char* w = static_cast<unsigned char*>(ws);
+        const unsigned cap = ws_cap(ws_bytes);
+        if ((st = cuda_status(cudaMemsetAsync(ws, 0, kWsCtlBytes, st_))) != RT_OK) return st;
+        const unsigned n_items = grid.x * grid.y * (unsigned)nwarps;
+#define RT_WS_LAUNCH(HR)                                                                                          \
+    do {                                                                                                          \
+        if ((st = ensure_smem(rt_fwd_p0_kernel<HR>, smem)) != RT_OK) return st;                                  \
+        if ((st = ensure_smem(rt_fwd_queue_kernel<HR>, smem)) != RT_OK) return st;                               \
+        const int threads = (int)(block.x * block.y);                                                             \
+        const unsigned g0 = std::min<unsigned>((unsigned)resident_ctas(rt_fwd_p0_kernel<HR>, threads, smem),     \
+                                               (n_items + nwarps - 1) / nwarps);                                  \
+        rt_fwd_p0_kernel<HR><<<g0, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr, plane,       \
+                                                       hstage, L.bx, L.by, (int)grid.x, n_items, w, cap);         \
+        g_launches++;                                                                                             \
+        const unsigned gq = std::min<unsigned>((unsigned)resident_ctas(rt_fwd_queue_kernel<HR>, threads, smem),  \
+                                               std::max(1u, (cap + 32u * nwarps - 1) / (32u * nwarps)));          \
+        for (int k = 1; k <= p->max_depth && cap > 0; ++k) {                                                      \
+            rt_fwd_queue_kernel<HR><<<gq, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr,       \
+                                                              plane, hstage, w, cap, k);                          \
+            g_launches++;                                                                                         \
+        }                                                                                                         \
+    } while (0)
+        if (hr) RT_WS_LAUNCH(true);
+        else RT_WS_LAUNCH(false);
+#undef RT_WS_LAUNCH
+        return cuda_status(cudaGetLastError());
+    }
 #define RT_FWD_LAUNCH(HR, CHK)                                                                                   \
     do {                                                                                                         \
         if ((st = ensure_smem(rt_fwd_kernel<HR, CHK>, smem)) != RT_OK) return st;                               \
@@ -876,6 +1023,21 @@ extern "C" rt_status rt_render_region(const rt_scene* s, const rt_camera* cam, c
                                       int32_t x0, int32_t y0, int32_t width, int32_t height, void* out_dev,
                                       size_t out_pitch_bytes, const rt_launch_config* cfg, void* stream) {
     return render_region(s, cam, p, x0, y0, width, height, out_dev, out_pitch_bytes, nullptr, cfg, stream);
+}
+
+extern "C" size_t rt_render_workspace_bytes(const rt_scene* s, const rt_render_params* p) {
+    if (!s || !p || p->width < 1 || p->height < 1) return 0;
+    const size_t px = (size_t)p->width * (size_t)p->height;
+    return kWsCtlBytes + 2 * kWsEntryBytes * ((px + 3) / 4);
+}
+
+extern "C" rt_status rt_render_ws(const rt_scene* s, const rt_camera* cam, const rt_render_params* p, void* out_dev,
+                                  size_t out_pitch_bytes, void* hitrec_dev, const rt_launch_config* cfg,
+                                  void* workspace_dev, size_t workspace_bytes, void* stream) {
+    if (!p || !workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) || workspace_bytes < kWsCtlBytes)
+        return RT_ERR_INVALID_ARG;
+    return render_region(s, cam, p, 0, 0, p->width, p->height, out_dev, out_pitch_bytes, hitrec_dev, cfg, stream,
+                         workspace_dev, workspace_bytes);
 }
 
 size_t rt_batch_workspace_bytes(int32_t n, const rt_scene* const* scenes, const rt_render_params* params,

@@ -545,11 +545,49 @@ __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& f
     }
 }
 
+// ---------------------------------------------------------------- bounce queues
+// Deferred paths of rt_render_ws.  A warp runs the bounce loop until its slowest
+// lane is done, so the few pixels whose reflection hits something again keep the
+// rest of their warp idle; instead, the first pass hands such a path over at its
+// bounce-1 hit, and later passes take the queued paths 32 at a time, one bounce
+// per pass, re-queueing those that hit again.  An entry holds the path state
+// exactly (FP32 values stored and reloaded), so a path's arithmetic -- and its
+// Philox counters, which depend on (pixel, bounce) only -- is the same wherever
+// it runs: images are bit-identical to the one-pass kernel.  A full queue is not
+// an error: the lane carries the path on itself.
+struct PathQueue {
+    float4* ent;      // 4 float4 per entry
+    unsigned* count;  // appends so far (may pass cap; only the first cap are stored)
+    unsigned cap;
+};
+
+// Entry: (o, T), (o_lo, pixel), (d, t), (accumulated colour, primitive id).
+__device__ __forceinline__ bool queue_push(const PathQueue& q, uint32_t pix, f3 o, f3 o_lo, f3 d, float T,
+                                           float3 out, int id, float t) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(q.count, (unsigned)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    const unsigned slot = base + (unsigned)__popc(mask & ((1u << lane) - 1u));
+    if (slot >= q.cap) return false;
+    float4* e = q.ent + (size_t)slot * 4;
+    e[0] = make_float4(o.x, o.y, o.z, T);
+    e[1] = make_float4(o_lo.x, o_lo.y, o_lo.z, __uint_as_float(pix));
+    e[2] = make_float4(d.x, d.y, d.z, t);
+    e[3] = make_float4(out.x, out.y, out.z, __int_as_float(id));
+    return true;
+}
+
 // Trace one pixel: bounce by bounce, closest hit (Section 3.4.1), then miss_add or
 // shade_step.  HITREC: write (id, t, vis_l) per bounce, id = -1 after the path ends.
+// dq (first pass of rt_render_ws): a path whose bounce-1 ray hits is pushed to dq
+// instead of being shaded here; *deferred tells the caller not to store the pixel.
 template <bool HITREC, bool CH, bool ACC = false>
 __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame& fr, int x, int y,
-                                              float* __restrict__ hr, size_t hr_plane, size_t hr_pix) {
+                                              float* __restrict__ hr, size_t hr_plane, size_t hr_pix,
+                                              const PathQueue* dq = nullptr, bool* deferred = nullptr) {
     const SceneHdr& h = *sc.hdr;
     const uint32_t pix = (uint32_t)y * (uint32_t)fr.W + (uint32_t)x;
     f3 o = mk3(fr.cam.x, fr.cam.y, fr.cam.z), o_lo = mk3(0.f, 0.f, 0.f);
@@ -569,6 +607,10 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
         if (id < 0) {
             miss_add(sc, d, T, out);
             break;
+        }
+        if (dq && k == 1 && queue_push(*dq, pix, o, o_lo, d, T, out, id, t)) {
+            *deferred = true;
+            return out;
         }
         shade_step<HITREC, CH, ACC>(sc, fr, pix, k, id, t, o, o_lo, d, T, out, hr,
                                     (size_t)k * (2 + h.nl) * hr_plane + hr_pix, hr_plane);
@@ -622,14 +664,75 @@ __device__ __forceinline__ void store_pixel(const Frame& fr, int x, int y, bool 
     }
 }
 
-// Trace pixel (x, y) of the frame and store it (store_pixel's rules).
+// Trace pixel (x, y) of the frame and store it (store_pixel's rules).  With dq, a
+// deferred pixel is not stored (F32) or stored with a placeholder that the pass
+// finishing its path overwrites (RGBA8, where four lanes share one store).
 template <bool HITREC, bool CH, bool ACC = false>
 __device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
                                              void* __restrict__ out, size_t pitch, float* __restrict__ hr,
-                                             size_t hr_plane) {
+                                             size_t hr_plane, const PathQueue* dq = nullptr) {
     float3 c = make_float3(0.f, 0.f, 0.f);
-    if (valid) c = trace_pixel<HITREC, CH, ACC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x);
-    store_pixel(fr, x, y, valid, c, out, pitch);
+    bool deferred = false;
+    if (valid)
+        c = trace_pixel<HITREC, CH, ACC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x, dq,
+                                         &deferred);
+    store_pixel(fr, x, y, valid && !(deferred && fr.fmt == RT_OUT_F32), c, out, pitch);
+}
+
+// Store one pixel on its own (the queued passes, whose lanes hold unrelated pixels).
+__device__ __forceinline__ void store_one(const Frame& fr, uint32_t pix, float3 c, void* __restrict__ out,
+                                          size_t pitch) {
+    const int x = (int)(pix % (uint32_t)fr.W), y = (int)(pix / (uint32_t)fr.W);
+    char* row = static_cast<char*>(out) + (size_t)(y - fr.ry0) * pitch;
+    if (fr.fmt == RT_OUT_F32)
+        *reinterpret_cast<float4*>(row + (size_t)(x - fr.rx0) * 16) = make_float4(c.x, c.y, c.z, 1.0f);
+    else
+        reinterpret_cast<uint32_t*>(row)[x - fr.rx0] = pack_rgba8(c);
+}
+
+// Pass k >= 1 of rt_render_ws for the entry e of queue k: shade the hit of bounce
+// k, then (below the depth limit) trace the reflected ray; a hit is pushed to nq
+// (queue k + 1) or, when that is full, shaded here to its end.  A path that ends
+// here stores its pixel and its hit record's trailing -1 ids.
+template <bool HITREC>
+__device__ __forceinline__ void trace_queued(const StagedScene& sc, const Frame& fr, const float4* __restrict__ e,
+                                             int k, const PathQueue& nq, void* __restrict__ out, size_t pitch,
+                                             float* __restrict__ hr, size_t hr_plane) {
+    const SceneHdr& h = *sc.hdr;
+    const int kq = k + 1;  // bounce of the entries of nq
+    const float4 e0 = e[0], e1 = e[1], e2 = e[2], e3 = e[3];
+    f3 o = mk3(e0.x, e0.y, e0.z), o_lo = mk3(e1.x, e1.y, e1.z), d = mk3(e2.x, e2.y, e2.z);
+    float T = e0.w, t = e2.w;
+    float3 c = make_float3(e3.x, e3.y, e3.z);
+    int id = __float_as_int(e3.w);
+    const uint32_t pix = __float_as_uint(e1.w);
+    const size_t hr_pix = pix;
+#pragma unroll 1
+    while (true) {
+        shade_step<HITREC, false, false>(sc, fr, pix, k, id, t, o, o_lo, d, T, c, hr,
+                                         (size_t)k * (2 + h.nl) * hr_plane + hr_pix, hr_plane);
+        if (k == fr.D) {
+            k = fr.D + 1;
+            break;
+        }
+        ++k;
+        id = closest_hit<false, false>(sc, o, d, t);
+        if (HITREC) {
+            float* rec = hr + (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
+            rec[0] = __int_as_float(id);
+            rec[hr_plane] = t;
+        }
+        if (id < 0) {
+            miss_add(sc, d, T, c);
+            break;
+        }
+        if (k == kq && queue_push(nq, pix, o, o_lo, d, T, c, id, t)) return;
+    }
+    if (HITREC) {
+        for (int kk = k + 1; kk <= fr.D; ++kk)
+            hr[(size_t)kk * (2 + h.nl) * hr_plane + hr_pix] = __int_as_float(-1);
+    }
+    store_one(fr, pix, c, out, pitch);
 }
 
 }  // namespace rtd

@@ -87,6 +87,11 @@ def lib():
         L.rt_scene_bytes.argtypes = [vp]
         L.rt_scene_bytes.restype = sz
         PP = C.POINTER(vp)
+        L.rt_render_ws.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), vp, sz, vp,
+                                   C.POINTER(LaunchConfig), vp, sz, vp]
+        L.rt_render_ws.restype = C.c_int
+        L.rt_render_workspace_bytes.argtypes = [vp, C.POINTER(RenderParams)]
+        L.rt_render_workspace_bytes.restype = sz
         L.rt_batch_workspace_bytes.argtypes = [i32, PP, C.POINTER(RenderParams), C.POINTER(LaunchConfig)]
         L.rt_batch_workspace_bytes.restype = sz
         L.rt_render_batch.argtypes = [i32, PP, C.POINTER(Camera), C.POINTER(RenderParams), PP,
@@ -291,11 +296,26 @@ def hitrec_bytes(dscene: DeviceScene, params: scenes.Params) -> int:
     return int(lib().rt_hitrec_bytes(dscene.handle, C.byref(params_struct(params))))
 
 
+def render_workspace_bytes(dscene: DeviceScene, params: scenes.Params) -> int:
+    """rt_render_workspace_bytes: the workspace rt_render_ws suggests for a frame."""
+    return int(lib().rt_render_workspace_bytes(dscene.handle, C.byref(params_struct(params))))
+
+
+def alloc_workspace(dscene: DeviceScene, params: scenes.Params, nbytes: int | None = None,
+                    device="cuda") -> torch.Tensor:
+    """A 256-byte aligned device buffer for rt_render_ws (torch allocations are)."""
+    n = render_workspace_bytes(dscene, params) if nbytes is None else int(nbytes)
+    ws = torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
 def render(dscene: DeviceScene, camera, params: scenes.Params, *, out: torch.Tensor | None = None,
            pitch: int | None = None, hitrec: torch.Tensor | None = None, launch=None,
-           stream=None) -> torch.Tensor:
-    """rt_render.  Returns the framebuffer: float32 [H, W, 4] (F32) or int32 [H, W]
-    holding 0xAABBGGRR (RGBA8)."""
+           stream=None, workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """rt_render, or rt_render_ws when a workspace (alloc_workspace) is given: the
+    same pixels, rendered in passes over compacted paths.  Returns the framebuffer:
+    float32 [H, W, 4] (F32) or int32 [H, W] holding 0xAABBGGRR (RGBA8)."""
     if out is None:
         out, pitch = alloc_output(params)
     elif pitch is None:
@@ -305,8 +325,15 @@ def render(dscene: DeviceScene, camera, params: scenes.Params, *, out: torch.Ten
     if hitrec is not None:
         assert hitrec.is_cuda and hitrec.numel() * hitrec.element_size() >= hitrec_bytes(dscene, params)
         hr = hitrec.data_ptr()
-    check("rt_render", lib().rt_render(dscene.handle, C.byref(cam), C.byref(prm), out.data_ptr(), pitch, hr,
-                                       C.byref(cfg) if cfg is not None else None, _stream(stream)))
+    cfgp = C.byref(cfg) if cfg is not None else None
+    if workspace is not None:
+        assert workspace.is_cuda and workspace.is_contiguous()
+        nb = workspace.numel() * workspace.element_size()
+        check("rt_render_ws", lib().rt_render_ws(dscene.handle, C.byref(cam), C.byref(prm), out.data_ptr(), pitch,
+                                                 hr, cfgp, workspace.data_ptr(), nb, _stream(stream)))
+    else:
+        check("rt_render", lib().rt_render(dscene.handle, C.byref(cam), C.byref(prm), out.data_ptr(), pitch, hr,
+                                           cfgp, _stream(stream)))
     if params.out_format != scenes.OUT_F32:
         return out[:, : params.width]
     return out

@@ -91,4 +91,12 @@ def test_host_validation_rejects_before_any_launch(L):
     p = rt.RenderParams()
     assert L.rt_render(None, C.byref(cam), C.byref(p), None, 0, None, None, None) == 1
     assert L.rt_hitrec_bytes(None, C.byref(p)) == 0
+    # queued render: no workspace, a misaligned one, one below the 256-byte control block
+    buf = (C.c_uint8 * 4096)()
+    base = (C.addressof(buf) + 255) // 256 * 256
+    assert L.rt_render_ws(None, C.byref(cam), C.byref(p), None, 0, None, None, None, 4096, None) == 1
+    assert L.rt_render_ws(None, C.byref(cam), C.byref(p), None, 0, None, None, base + 16, 2048, None) == 1
+    assert L.rt_render_ws(None, C.byref(cam), C.byref(p), None, 0, None, None, base, 255, None) == 1
+    assert L.rt_render_ws(None, C.byref(cam), C.byref(p), None, 0, None, None, base, 2048, None) == 1
+    assert L.rt_render_workspace_bytes(None, C.byref(p)) == 0
     assert L.rt_launch_count() == before
