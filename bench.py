@@ -172,16 +172,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name: str):
-    """DRAM bytes per launch of the forward kernel from the committed ncu summary,
-    only if it was taken on the current kernel sources."""
+def recorded_traffic(workload_name: str, kernel: str = "rt_fwd_kernel"):
+    """DRAM bytes per frame of the forward kernel(s) from the committed ncu summary
+    ("rt_fwd_kernel": the one-pass launch; "rt_render_ws": the sum over the first
+    pass and the D queue passes of one frame), only if it was taken on the current
+    kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     want = kernel_source_hash()
     for ln in open(path):
         f = ln.split()
-        if len(f) >= 4 and not ln.startswith("#") and f[0] == "rt_fwd_kernel" and f[1] == want \
+        if len(f) >= 4 and not ln.startswith("#") and f[0] == kernel and f[1] == want \
                 and f[2] == workload_name:
             return float(f[3])
     return None
@@ -224,9 +226,11 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     from paper_2305_07450_b300 import autotune
     launch = autotune.tune_render(ds, w.scene, w.camera, w.params, stream=stream)  # untimed; cached
+    # rt_render_ws when the tuner chose the queued passes: its workspace is resident
+    wsbuf = rt.alloc_workspace(ds, w.params, device=dev) if launch.get("queued") else None
 
     def step():
-        rt.render(ds, w.camera, w.params, out=out, pitch=pitch, launch=launch, stream=stream)
+        rt.render(ds, w.camera, w.params, out=out, pitch=pitch, launch=launch, stream=stream, workspace=wsbuf)
 
     for _ in range(args.warmup):
         step()
@@ -299,8 +303,9 @@ def run_ours(args):
             rec["roofline"] = {
                 "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
                 "frac": achieved / peak_max,
-                "traffic": recorded_traffic(w.name),
-                "kernel": "rt_fwd_kernel",
+                "traffic": recorded_traffic(w.name, "rt_render_ws" if wsbuf is not None else "rt_fwd_kernel"),
+                "kernel": ("rt_fwd_p0_kernel + rt_fwd_queue_kernel x D (rt_render_ws: one frame = 1 + D launches, "
+                           "timed together)" if wsbuf is not None else "rt_fwd_kernel"),
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)",
                 "frac_at_measured_clock": (achieved / (sm_count * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                            if clocks.get("sm_mhz") else None),
@@ -358,10 +363,11 @@ def extras(args, dev, stream):
     b = rt.Batch(dss, [w.camera for w in ws], [w.params for w in ws], launch=blaunch, stream=stream)
     ms_graph = _time_device(lambda: b.launch(stream), stream, 5)
     flaunch = [autotune.tune_render(d, w.scene, w.camera, w.params, stream=stream, reps=1) for w, d in zip(ws, dss)]
+    fws = [rt.alloc_workspace(d, w.params) if fl.get("queued") else None for w, d, fl in zip(ws, dss, flaunch)]
 
     def seq():
-        for w, d, o, pt, fl in zip(ws, dss, b.outs, b.pitches, flaunch):
-            rt.render(d, w.camera, w.params, out=o, pitch=pt, launch=fl, stream=stream)
+        for w, d, o, pt, fl, wb in zip(ws, dss, b.outs, b.pitches, flaunch, fws):
+            rt.render(d, w.camera, w.params, out=o, pitch=pt, launch=fl, stream=stream, workspace=wb)
     ms_seq = _time_device(seq, stream, 3)
     px = sum(w.params.width * w.params.height for w in ws)
     out["batch64"] = {"workload": "64 seeded scenes, 8-512 spheres, 1-4 lights, depth 1-6, 256^2..1080p, F32",
@@ -427,8 +433,9 @@ def bvh_extra(dev, stream):
         o1, pitch = rt.alloc_output(w.params, device=dev)
         o2, _ = rt.alloc_output(w.params, device=dev)
         bf = autotune.tune_render(ds, w.scene, w.camera, w.params, stream=stream)
-        ms_bf = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o1, pitch=pitch, launch=bf, stream=stream),
-                             stream, 5)
+        wbf = rt.alloc_workspace(ds, w.params) if bf.get("queued") else None
+        ms_bf = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o1, pitch=pitch, launch=bf, stream=stream,
+                                               workspace=wbf), stream, 5)
         best = None
         for cand in ({"block_x": 16, "block_y": 8}, {"block_x": 8, "block_y": 8}, {"block_x": 32, "block_y": 4},
                      {"block_x": 8, "block_y": 16}, {"block_x": 16, "block_y": 16}):
@@ -541,8 +548,9 @@ def run_reference(args):
 
 
 def profile_render(args):
-    """Only rt_render of the workload, warmup + steps times, with the library's default
-    launch (16x8 pixels, TMA staging): the program ncu captures for the forward kernel."""
+    """Only the render of the workload, warmup + steps frames, with the library's
+    default launch (16x8 pixels, TMA staging): rt_render, or with --queued rt_render_ws
+    (1 + D launches per frame): the program ncu captures for the forward kernels."""
     import torch
     from paper_2305_07450_b300 import rt
     w = workload(args.workload)
@@ -551,11 +559,13 @@ def profile_render(args):
     launch = {"accel": 1} if args.accel else None
     if args.accel:
         ds.build_bvh()
+    wsbuf = rt.alloc_workspace(ds, w.params) if args.queued else None
     for _ in range(args.warmup + args.steps):
-        rt.render(ds, w.camera, w.params, out=out, pitch=pitch, launch=launch)
+        rt.render(ds, w.camera, w.params, out=out, pitch=pitch, launch=launch, workspace=wsbuf)
     torch.cuda.synchronize()
     assert rt.device_errors() == 0
-    print(json.dumps({"profile_render": w.name, "accel": bool(args.accel), "launches": args.warmup + args.steps}))
+    print(json.dumps({"profile_render": w.name, "accel": bool(args.accel), "queued": bool(args.queued),
+                      "frames": args.warmup + args.steps}))
 
 
 def profile_batch(args):
@@ -585,6 +595,7 @@ def main(argv=None):
     ap.add_argument("--profile-render", action="store_true",
                     help="only render the workload (warmup + steps launches, default launch), for ncu")
     ap.add_argument("--accel", action="store_true", help="with --profile-render: through the sphere hierarchy")
+    ap.add_argument("--queued", action="store_true", help="with --profile-render: rt_render_ws (queued passes)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="only launch the 64-scene batch graph --warmup + --steps times (a profiling target)")
     args = ap.parse_args(argv)

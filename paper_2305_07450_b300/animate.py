@@ -31,6 +31,8 @@ class Animation:
         self.plane_t = None if sc.plane is None else torch.from_numpy(self.plane_rec).to(device)
         self.lights_t = torch.from_numpy(np.ascontiguousarray(sc.lights, np.float32)).to(device)
         self.out, self.pitch = rt.alloc_output(workload.params, device=device)
+        self.ws = (rt.alloc_workspace(self.ds, workload.params, device=device)
+                   if launch is not None and dict(launch).get("queued") else None)
         self.host = torch.empty(self.out.shape, dtype=self.out.dtype, pin_memory=True)
         self.frames = 0
 
@@ -41,7 +43,7 @@ class Animation:
                        restitution=self.restitution, steps=self.substeps, stream=self.stream)
         self.ds.update(spheres=self.spheres, plane=self.plane_t, lights=self.lights_t, stream=self.stream)
         rt.render(self.ds, self.w.camera, self.w.params, out=self.out, pitch=self.pitch, launch=self.launch,
-                  stream=self.stream)
+                  stream=self.stream, workspace=self.ws)
         self.frames += 1
         if readback:
             self.host.copy_(self.out, non_blocking=True)

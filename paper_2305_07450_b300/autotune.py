@@ -1,4 +1,5 @@
-"""Autotuner of the render kernels' launch shape (CTA pixel tile, staging mode).
+"""Autotuner of the render kernels' launch shape (CTA pixel tile, staging mode,
+one pass (rt_render) or queued passes (rt_render_ws)).
 
 A launch configuration is measured, not guessed: every candidate CTA shape is
 timed with CUDA events on the caller's stream (median of a few launches after a
@@ -107,24 +108,33 @@ def _time(fn, stream, reps: int) -> float:
 
 
 def tune_render(dscene: rt.DeviceScene, scene: scenes.Scene, camera, params: scenes.Params, *, reps: int = 3,
-                candidates=FWD_CANDIDATES, stream=None, force: bool = False) -> dict:
-    """Best launch for rt_render of this frame (measured, then cached)."""
+                candidates=FWD_CANDIDATES, stream=None, force: bool = False, queued: bool = True) -> dict:
+    """Best launch for one frame (measured, then cached): CTA tile and staging
+    mode, through rt_render or (queued=True) also rt_render_ws -- the returned
+    launch then holds "queued": 1, and the caller passes a workspace
+    (rt.alloc_workspace) or lets rt.render allocate one."""
     key = key_for(scene, params, "fwd")
     hit = None if force else lookup(key)
     if hit is not None:
         return hit["launch"]
     stream = stream or torch.cuda.current_stream()
     out, pitch = rt.alloc_output(params)
+    ws = rt.alloc_workspace(dscene, params) if queued else None
     results = {}
     for bx, by in candidates:
-        for staging in (1, 2):
+        # staging 1 / 2 through rt_render; 1 / 2 through rt_render_ws (queued, q = 1)
+        for staging, q in ((1, 0), (2, 0)) + (((1, 1), (2, 1)) if queued else ()):
             launch = {"block_x": bx, "block_y": by, "staging": staging}
-            results[(bx, by, staging)] = _time(
-                lambda: rt.render(dscene, camera, params, out=out, pitch=pitch, launch=launch, stream=stream),
+            results[(bx, by, staging, q)] = _time(
+                lambda: rt.render(dscene, camera, params, out=out, pitch=pitch, launch=launch, stream=stream,
+                                  workspace=ws if q else None),
                 stream, reps)
-    (bx, by, staging), ms = min(results.items(), key=lambda kv: kv[1])
-    entry = {"launch": {"block_x": bx, "block_y": by, "staging": staging}, "ms": ms,
-             "candidates": {f"{a}x{b}/s{c}": round(v, 4) for (a, b, c), v in results.items()}}
+    (bx, by, staging, q), ms = min(results.items(), key=lambda kv: kv[1])
+    best = {"block_x": bx, "block_y": by, "staging": staging}
+    if q:
+        best["queued"] = 1
+    entry = {"launch": best, "ms": ms,
+             "candidates": {f"{a}x{b}/s{c}{'/q' if d else ''}": round(v, 4) for (a, b, c, d), v in results.items()}}
     _store(key, entry)
     return entry["launch"]
 

@@ -161,8 +161,10 @@ def launch_struct(launch) -> LaunchConfig | None:
     if launch is None:
         return None
     s = LaunchConfig()
+    fields = {f[0] for f in LaunchConfig._fields_}
     for k, v in dict(launch).items():
-        setattr(s, k, int(v))
+        if k in fields:  # "queued" (the autotuner's choice of rt_render_ws) is not a field
+            setattr(s, k, int(v))
     return s
 
 
@@ -313,9 +315,13 @@ def alloc_workspace(dscene: DeviceScene, params: scenes.Params, nbytes: int | No
 def render(dscene: DeviceScene, camera, params: scenes.Params, *, out: torch.Tensor | None = None,
            pitch: int | None = None, hitrec: torch.Tensor | None = None, launch=None,
            stream=None, workspace: torch.Tensor | None = None) -> torch.Tensor:
-    """rt_render, or rt_render_ws when a workspace (alloc_workspace) is given: the
-    same pixels, rendered in passes over compacted paths.  Returns the framebuffer:
-    float32 [H, W, 4] (F32) or int32 [H, W] holding 0xAABBGGRR (RGBA8)."""
+    """rt_render, or rt_render_ws when a workspace (alloc_workspace) is given -- the
+    same pixels, rendered in passes over compacted paths.  A launch with
+    "queued": 1 (the autotuner's choice) and no workspace gets one allocated here.
+    Returns the framebuffer: float32 [H, W, 4] (F32) or int32 [H, W] holding
+    0xAABBGGRR (RGBA8)."""
+    if workspace is None and launch is not None and dict(launch).get("queued"):
+        workspace = alloc_workspace(dscene, params)
     if out is None:
         out, pitch = alloc_output(params)
     elif pitch is None:
