@@ -69,7 +69,7 @@ static SceneView view_of(const rt_scene* s) {
 // once per CTA.  Register budget 80 (6 CTAs of 128 threads per SM): measured on
 // B300 at 4K as 16.05 ms against 16.25 (96), 16.01 (72), 16.02 (64) and slower
 // at 104 / 112 / 128; the spills it causes sit outside the sphere loops.
-template <bool HITREC, bool CH>
+template <bool HITREC, bool CH, int FM>
 __global__ void __maxnreg__(80) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                      size_t pitch, float* __restrict__ hr, size_t hr_plane,
                                                      int staging, int block_x, int block_y) {
@@ -93,7 +93,7 @@ __global__ void __maxnreg__(80) rt_fwd_kernel(const SceneView sv, const Frame fr
     const int x = fr.rx0 + blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
     const int y = fr.ry0 + blockIdx.y * block_y + (warp / wpr) * 4 + (lane >> 3);
     const bool valid = x < fr.rx1 && y < fr.ry1;
-    render_pixel<HITREC, CH>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
+    render_pixel<HITREC, CH, false, FM>(sc, fr, x, y, valid, out, pitch, hr, hr_plane);
 }
 
 // ============================================================ queued render (rt_render_ws)
@@ -121,7 +121,7 @@ __device__ __forceinline__ PathQueue ws_queue(unsigned char* ws, unsigned cap, i
 // First pass: persistent CTAs (one per resident slot) stage the scene once; each
 // warp claims 8 x 4 pixel patches (in the order of block_x x block_y tiles) and
 // traces them, pushing paths whose bounce-1 ray hits to queue 1.
-template <bool HITREC>
+template <bool HITREC, int FM>
 __global__ void __maxnreg__(80) rt_fwd_p0_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                  size_t pitch, float* __restrict__ hr, size_t hr_plane, int staging,
                                                  int block_x, int block_y, int tiles_x, unsigned n_items,
@@ -151,13 +151,14 @@ __global__ void __maxnreg__(80) rt_fwd_p0_kernel(const SceneView sv, const Frame
         const int x = fr.rx0 + (tile % tiles_x) * block_x + (wi % wpr) * 8 + (lane & 7);
         const int y = fr.ry0 + (tile / tiles_x) * block_y + (wi / wpr) * 4 + (lane >> 3);
         const bool valid = x < fr.rx1 && y < fr.ry1;
-        render_pixel<HITREC, false>(sc, fr, x, y, valid, out, pitch, hr, hr_plane, fr.D >= 1 ? &q1 : nullptr);
+        render_pixel<HITREC, false, false, FM>(sc, fr, x, y, valid, out, pitch, hr, hr_plane,
+                                              fr.D >= 1 ? &q1 : nullptr);
     }
 }
 
 // Pass k >= 1: persistent CTAs; each warp claims 32 entries of queue k at a time.
 // CTAs beyond the ones the queue's length needs return before staging.
-template <bool HITREC>
+template <bool HITREC, int FM>
 __global__ void __maxnreg__(80) rt_fwd_queue_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                     size_t pitch, float* __restrict__ hr, size_t hr_plane,
                                                     int staging, unsigned char* __restrict__ ws, unsigned cap, int k) {
@@ -186,7 +187,7 @@ __global__ void __maxnreg__(80) rt_fwd_queue_kernel(const SceneView sv, const Fr
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n) break;
         const unsigned i = base + (unsigned)lane;
-        if (i < n) trace_queued<HITREC>(sc, fr, cur.ent + (size_t)i * 4, k, nxt, out, pitch, hr, hr_plane);
+        if (i < n) trace_queued<HITREC, FM>(sc, fr, cur.ent + (size_t)i * 4, k, nxt, out, pitch, hr, hr_plane);
         __syncwarp();
     }
 }
@@ -517,13 +518,16 @@ int max_smem_optin() {
 
 // The whole geometry table is staged unless it does not fit (or the tiled loop is
 // forced with staging = 3).
+constexpr size_t kStaticSmemReserve = 28 * 1024;
 size_t stage_smem_bytes(bool chunked, int ns_pad, int nwarps) {
     return chunked ? sizeof(SceneHdr) + (size_t)nwarps * kChunk * 16 : sizeof(SceneHdr) + (size_t)ns_pad * 16;
 }
 
 bool use_tiled_loop(const Launch& L, int ns_pad) {
     if (L.staging == 3) return true;
-    return stage_smem_bytes(false, ns_pad, 0) + 4096 > (size_t)(max_smem_optin() - 1024);
+    // room left for the kernels' static shared memory (the shadow test's 24 KB of
+    // segment vectors and the barriers)
+    return stage_smem_bytes(false, ns_pad, 0) + kStaticSmemReserve > (size_t)max_smem_optin();
 }
 
 // Resident CTAs of `kernel` on the current device (threads per CTA, dynamic shared
@@ -549,8 +553,10 @@ int resident_ctas(K kernel, int threads, size_t smem) {
 
 template <typename K>
 rt_status ensure_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return RT_OK;
-    const int cap = max_smem_optin() - 1024;  // static shared memory of the kernels
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return RT_ERR_CUDA;
+    if (bytes + fa.sharedSizeBytes <= 48 * 1024) return RT_OK;
+    const int cap = max_smem_optin() - (int)fa.sharedSizeBytes;  // what the kernel's static shared memory leaves
     if ((long long)bytes > cap) return RT_ERR_UNSUPPORTED;
     return cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
 }
@@ -972,41 +978,54 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         const unsigned cap = ws_cap(ws_bytes);
         if ((st = cuda_status(cudaMemsetAsync(ws, 0, kWsCtlBytes, st_))) != RT_OK) return st;
         const unsigned n_items = grid.x * grid.y * (unsigned)nwarps;
-#define RT_WS_LAUNCH(HR)                                                                                          \
+        // the shading path compiled in: the line filter from kFilterMinPad spheres on
+        const bool filt = s->ns_pad >= kFilterMinPad;
+#define RT_WS_LAUNCH(HR, FM)                                                                                      \
     do {                                                                                                          \
-        if ((st = ensure_smem(rt_fwd_p0_kernel<HR>, smem)) != RT_OK) return st;                                  \
-        if ((st = ensure_smem(rt_fwd_queue_kernel<HR>, smem)) != RT_OK) return st;                               \
+        if ((st = ensure_smem(rt_fwd_p0_kernel<HR, FM>, smem)) != RT_OK) return st;                              \
+        if ((st = ensure_smem(rt_fwd_queue_kernel<HR, FM>, smem)) != RT_OK) return st;                           \
         const int threads = (int)(block.x * block.y);                                                             \
-        const unsigned g0 = std::min<unsigned>((unsigned)resident_ctas(rt_fwd_p0_kernel<HR>, threads, smem),     \
+        const unsigned g0 = std::min<unsigned>((unsigned)resident_ctas(rt_fwd_p0_kernel<HR, FM>, threads, smem), \
                                                (n_items + nwarps - 1) / nwarps);                                  \
-        rt_fwd_p0_kernel<HR><<<g0, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr, plane,       \
-                                                       hstage, L.bx, L.by, (int)grid.x, n_items, w, cap);         \
+        rt_fwd_p0_kernel<HR, FM><<<g0, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr, plane,   \
+                                                           hstage, L.bx, L.by, (int)grid.x, n_items, w, cap);     \
         g_launches++;                                                                                             \
-        const unsigned gq = std::min<unsigned>((unsigned)resident_ctas(rt_fwd_queue_kernel<HR>, threads, smem),  \
-                                               std::max(1u, (cap + 32u * nwarps - 1) / (32u * nwarps)));          \
+        const unsigned gq =                                                                                       \
+            std::min<unsigned>((unsigned)resident_ctas(rt_fwd_queue_kernel<HR, FM>, threads, smem),               \
+                               std::max(1u, (cap + 32u * nwarps - 1) / (32u * nwarps)));                          \
         for (int k = 1; k <= p->max_depth && cap > 0; ++k) {                                                      \
-            rt_fwd_queue_kernel<HR><<<gq, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr,       \
-                                                              plane, hstage, w, cap, k);                          \
+            rt_fwd_queue_kernel<HR, FM><<<gq, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr,   \
+                                                                  plane, hstage, w, cap, k);                      \
             g_launches++;                                                                                         \
         }                                                                                                         \
     } while (0)
-        if (hr) RT_WS_LAUNCH(true);
-        else RT_WS_LAUNCH(false);
+        if (hr) {
+            if (filt) RT_WS_LAUNCH(true, 1);
+            else RT_WS_LAUNCH(true, 0);
+        } else {
+            if (filt) RT_WS_LAUNCH(false, 1);
+            else RT_WS_LAUNCH(false, 0);
+        }
 #undef RT_WS_LAUNCH
         return cuda_status(cudaGetLastError());
     }
-#define RT_FWD_LAUNCH(HR, CHK)                                                                                   \
+#define RT_FWD_LAUNCH(HR, CHK, FM)                                                                               \
     do {                                                                                                         \
-        if ((st = ensure_smem(rt_fwd_kernel<HR, CHK>, smem)) != RT_OK) return st;                               \
-        rt_fwd_kernel<HR, CHK><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr, plane, \
-                                                          hstage, L.bx, L.by);                                  \
+        if ((st = ensure_smem(rt_fwd_kernel<HR, CHK, FM>, smem)) != RT_OK) return st;                           \
+        rt_fwd_kernel<HR, CHK, FM><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr,    \
+                                                              plane, hstage, L.bx, L.by);                       \
     } while (0)
+    // the shading path compiled in: the line filter from kFilterMinPad spheres on
+    // (the tiled loop keeps the segment test)
+    const bool filt = !chunked && s->ns_pad >= kFilterMinPad;
     if (hr) {
-        if (chunked) RT_FWD_LAUNCH(true, true);
-        else RT_FWD_LAUNCH(true, false);
+        if (chunked) RT_FWD_LAUNCH(true, true, 0);
+        else if (filt) RT_FWD_LAUNCH(true, false, 1);
+        else RT_FWD_LAUNCH(true, false, 0);
     } else {
-        if (chunked) RT_FWD_LAUNCH(false, true);
-        else RT_FWD_LAUNCH(false, false);
+        if (chunked) RT_FWD_LAUNCH(false, true, 0);
+        else if (filt) RT_FWD_LAUNCH(false, false, 1);
+        else RT_FWD_LAUNCH(false, false, 0);
     }
 #undef RT_FWD_LAUNCH
     g_launches++;
@@ -1177,8 +1196,8 @@ rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_r
     const int G = grad_count(s->ns, s->nl);
     const int nwarps = (L.bx * L.by) / 32;
     const size_t tabs = (size_t)nwarps * G * 4;
-    const bool chunked = L.staging == 3 || stage_smem_bytes(false, s->ns_pad, nwarps) + tabs + 4096 >
-                                               (size_t)(max_smem_optin() - 1024);
+    const bool chunked = L.staging == 3 || stage_smem_bytes(false, s->ns_pad, nwarps) + tabs + kStaticSmemReserve >
+                                               (size_t)max_smem_optin();
     const size_t smem = stage_smem_bytes(chunked, s->ns_pad, nwarps) + tabs;
     const int hstage = L.staging == 2 ? 2 : 1;
     const Frame fr = make_frame(s, cam, p);

@@ -208,6 +208,147 @@ __device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, u
     return __all_sync(mask, done);
 }
 
+// Line filter in front of the segment test.  The segment o + u V (u in [0, 1]) can
+// only be blocked by a sphere that the infinite line through it passes within r
+// of: D^2 = |oc|^2 - (oc.V^)^2 < r^2 with V^ the unit vector along V.  Per sphere
+// pair the filter forms |oc|^2 (3 packed FMAs, shared by the group's segments),
+// and per segment t' = oc.V^ (3) and g = t'^2 + K2 r^2 - K1 |oc|^2 (1): 4 packed
+// instructions instead of the segment test's 8 packed plus 2 scalar.  Where g > 0
+// or is NaN ("maybe"), the segment test runs as before and decides; elsewhere it
+// would have said "not blocked", so every verdict is the segment test's, bit for
+// bit.  Why g <= 0 implies that (u = 2^-24; oc, V, r^2 the FP32 values both tests
+// use): the segment test's e is negative only if D^2 < r^2 (1 + 9u) (q = oc - u V
+// carries one rounding per component, e three).  V^ = V rsqrt(S), S = fl(V.V), is
+// within 4u of the unit vector componentwise, so the FP32 t' is within 7u |oc| of
+// oc.V^ and t'^2 >= |oc|^2 - D^2 - 14u |oc|^2; the filter's roundings cost at most
+// 5u |oc|^2 + 3u r^2.  With K1 = 1 - 64u and K2 = 1 + 64u, e < 0 gives
+// g > 45u |oc|^2 + 54u r^2 > 0.  The bound needs finite arithmetic: a pair whose
+// |oc|^2 exceeds 2^100 is flagged too, and a group whose S leaves [2^-60, 2^100]
+// for some lane takes the segment test throughout.  The flags are kept as the AND
+// of sign bits ("certainly clear" = every value negative), so NaN and +inf count
+// as "maybe".  W and -V of each segment wait in shared memory (24 floats per
+// thread, written once per group) for the pairs that need the segment test.
+constexpr int kFilterMinPad = 128;  // smaller sphere tables keep the segment test alone
+constexpr float kFiltK1 = 1.0f - 64.0f / 16777216.0f;
+constexpr float kFiltK2 = 1.0f + 64.0f / 16777216.0f;
+constexpr int kSegStride = 256;  // threads per CTA at most (the launch shapes allow 256)
+
+// One array per kernel (namespace scope): every instantiation of the shadow test
+// shares it.
+__shared__ float s_seg[6 * kShadowGroup * kSegStride];
+
+struct SegFilt {  // V^ of a segment in both halves
+    float2 vx, vy, vz;
+};
+
+// Segment test of pair q (spheres 2q, 2q + 1 of geo) against the R segments, the
+// operations of occluded_block; W and -V from shared memory (seg[k * kSegStride],
+// k = 6 r + (0..2: W, 3..5: -V)).
+template <int R>
+__device__ __forceinline__ void pair_exact(const float4* __restrict__ geo, int q, const RayPair& o2,
+                                           const float* seg, uint32_t (&acc)[kShadowGroup]) {
+    const float4 A = geo[2 * q], B = geo[2 * q + 1];
+    const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
+    const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
+    const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
+    const float2 nr = make_float2(B.z, B.w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float* g = seg + 6 * r * kSegStride;
+        const float wx = g[0], wy = g[kSegStride], wz = g[2 * kSegStride];
+        const float2 t = fma2(ocy, dup2(wy), mul2(ocz, dup2(wz)));
+        const float2 u = make_float2(fma_sat(ocx.x, wx, t.x), fma_sat(ocx.y, wx, t.y));
+        const float2 qx = fma2(u, dup2(g[3 * kSegStride]), ocx), qy = fma2(u, dup2(g[4 * kSegStride]), ocy),
+                     qz = fma2(u, dup2(g[5 * kSegStride]), ocz);
+        const float2 e = fma2(qx, qx, fma2(qy, qy, fma2(qz, qz, nr)));
+        acc[r] |= __float_as_uint(e.x) | __float_as_uint(e.y);
+    }
+}
+
+// One block of kPad spheres through the filter; the segment test for the pairs
+// some lane flags.  Returns true when every segment of every lane in `mask` is
+// blocked (checked only after a segment test ran: the filter alone blocks nothing).
+template <int R>
+__device__ __forceinline__ bool occluded_block_filtered(const float4* __restrict__ geo, unsigned mask,
+                                                        const RayPair& o2, const SegFilt (&sf)[kShadowGroup],
+                                                        const float* seg, uint32_t (&acc)[kShadowGroup]) {
+    uint32_t clear[kPad / 2];
+#pragma unroll
+    for (int q = 0; q < kPad / 2; ++q) {
+        const float4 A = geo[2 * q], B = geo[2 * q + 1];
+        const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
+        const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
+        const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
+        const float2 oc2 = fma2(ocx, ocx, fma2(ocy, ocy, mul2(ocz, ocz)));
+        // K2 r^2 - K1 |oc|^2 (B.zw = -r^2), and |oc|^2 - 2^100 (positive: too large)
+        const float2 c = fma2(oc2, dup2(-kFiltK1), mul2(make_float2(B.z, B.w), dup2(-kFiltK2)));
+        const float2 big = add2(oc2, dup2(-0x1p100f));
+        clear[q] = __float_as_uint(big.x) & __float_as_uint(big.y);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 t = fma2(ocx, sf[r].vx, fma2(ocy, sf[r].vy, mul2(ocz, sf[r].vz)));
+            const float2 g = fma2(t, t, c);
+            clear[q] &= __float_as_uint(g.x) & __float_as_uint(g.y);
+        }
+    }
+    if (__all_sync(mask, ((clear[0] & clear[1] & clear[2] & clear[3]) >> 31) != 0)) return false;
+    // pairs some lane flags, one warp-uniform bit each; one copy of the segment test
+    uint32_t need = 0;
+#pragma unroll
+    for (int q = 0; q < kPad / 2; ++q) need |= __all_sync(mask, (clear[q] >> 31) != 0) ? 0u : (1u << q);
+#pragma unroll 1
+    while (need) {
+        const int q = __ffs(need) - 1;
+        need &= need - 1u;
+        pair_exact<R>(geo, q, o2, seg, acc);
+    }
+    bool done = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) done = done && (acc[r] >> 31);
+    return __all_sync(mask, done);
+}
+
+// The filtered sphere loop of one group, out of line: inlined into the shading
+// code its registers and the caller's live state spilled inside the sphere loop
+// (ncu: 2e8 local loads and stores per 1080p launch); called, the caller's state is
+// saved once per group.  vh[3 r .. 3 r + 2] = V^ of segment r (zero for segments
+// already blocked); blocked_in / the result: bit r = segment r blocked.  The
+// caller has written W and -V to seg (shared memory).  exact_only: the segment
+// test for every pair (a group for which the filter's bound is not established).
+template <int R>
+__device__ __noinline__ uint32_t occluded_filtered(const float4* __restrict__ geo, int n, unsigned mask, f3 o,
+                                                   const float* __restrict__ vh, uint32_t blocked_in,
+                                                   const float* seg, bool exact_only) {
+    const RayPair o2 = ray_pair(o);
+    SegFilt sf[kShadowGroup];
+    uint32_t acc[kShadowGroup];
+#pragma unroll
+    for (int r = 0; r < kShadowGroup; ++r) {
+        acc[r] = (blocked_in >> r) & 1u ? 0x80000000u : 0u;
+        sf[r] = r < R ? SegFilt{dup2(vh[3 * r]), dup2(vh[3 * r + 1]), dup2(vh[3 * r + 2])}
+                      : SegFilt{dup2(0.f), dup2(0.f), dup2(0.f)};
+    }
+    if (exact_only) {  // the filter's bound does not hold for some lane: the segment test throughout
+#pragma unroll 1
+        for (int i0 = 0; i0 < n; i0 += kPad) {
+#pragma unroll 1
+            for (int q = 0; q < kPad / 2; ++q) pair_exact<R>(geo + i0, q, o2, seg, acc);
+            bool done = true;
+#pragma unroll
+            for (int r = 0; r < R; ++r) done = done && (acc[r] >> 31);
+            if (__all_sync(mask, done)) break;
+        }
+    } else {
+#pragma unroll 1
+        for (int i0 = 0; i0 < n; i0 += kPad)
+            if (occluded_block_filtered<R>(geo + i0, mask, o2, sf, seg, acc)) break;
+    }
+    uint32_t out = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out |= (acc[r] >> 31) << r;
+    return out;
+}
+
 // Segment r is o + u V_r (u in [0, 1]) with -V_r = nv[r] and W_r = w[r].  occ[r]
 // enters true for unused slots (and leaves true for blocked segments).  The plane is
 // tested first: a segment it blocks enters the sphere loop as blocked (the verdict
@@ -235,14 +376,13 @@ __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, cons
     } else {
         const unsigned mask = __activemask();
         const RayPair o2 = ray_pair(o);
-        SegPair sg[kShadowGroup];
         uint32_t acc[kShadowGroup];
 #pragma unroll
-        for (int r = 0; r < kShadowGroup; ++r) {
-            sg[r] = seg_pair(w[r], nv[r]);
-            acc[r] = occ[r] ? 0x80000000u : 0u;
-        }
+        for (int r = 0; r < kShadowGroup; ++r) acc[r] = occ[r] ? 0x80000000u : 0u;
         if constexpr (CH) {
+            SegPair sg[kShadowGroup];
+#pragma unroll
+            for (int r = 0; r < kShadowGroup; ++r) sg[r] = seg_pair(w[r], nv[r]);
             bool stop = false;
 #pragma unroll 1
             for (int c0 = 0; c0 < n && !stop; c0 += kChunk) {
@@ -257,6 +397,9 @@ __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, cons
                 }
             }
         } else {
+            SegPair sg[kShadowGroup];
+#pragma unroll
+            for (int r = 0; r < kShadowGroup; ++r) sg[r] = seg_pair(w[r], nv[r]);
 #pragma unroll 1
             for (int i0 = 0; i0 < n; i0 += kPad)
                 if (occluded_block<R>(sc.geo + i0, mask, o2, sg, acc)) break;
@@ -415,6 +558,118 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
     return out;
 }
 
+// shade_hit for the staged brute-force kernels: the same shading, rays, Philox
+// counters and attribution, with the group's segments set up by a loop (one copy
+// of the sample code) that writes W and -V to shared memory and the unit vectors
+// for the filter to a local array, and every group tested by occluded_filtered.
+template <bool HITREC>
+__device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, const Frame& fr, uint32_t pix, int k,
+                                                     f3 p, f3 p_lo, f3 n, f3 po, f3 d, float ks, float e,
+                                                     float* __restrict__ hr, size_t hr_k, size_t hr_plane) {
+    const SceneHdr& h = *sc.hdr;
+    HitShade out{fr.ka, 0.0f};
+    uint32_t lit = 0;
+    int total = 0;
+#pragma unroll 1
+    for (int li = 0; li < h.nl; ++li) {
+        const f3 lh = normalize_rn(sub(sub(xyz(h.light_p[li]), p), p_lo));
+        if (dot(n, lh) > 0.0f) {
+            lit |= 1u << li;
+            total += rays_of_light(fr, h.light_s[li]);
+        }
+        if (HITREC) hr[hr_k + (size_t)(2 + li) * hr_plane] = 0.0f;
+    }
+    // (cl, cs): light and sample of the next result to attribute; (l, s): of the
+    // next segment to set up
+    int cl = lit ? __ffs(lit) - 1 : 0, cs = 0, cnt = 0;
+    int l = cl, s = 0;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    int done = 0;
+    const unsigned mask = __activemask();
+    float* seg = s_seg + (threadIdx.x + blockDim.x * threadIdx.y);
+    const bool plane = h.has_plane != 0;
+    const f3 pn = xyz(h.plane_g);
+    const float num = -(dot(po, pn) + h.plane_g.w);
+#pragma unroll 1
+    while (true) {
+        const int kr = min(kShadowGroup, total - done);
+        const int R = (int)__reduce_max_sync(mask, (unsigned)kr);
+        if (R == 0) break;
+        float vh[3 * kShadowGroup];
+        uint32_t blocked = 0;
+        bool ok = true;
+#pragma unroll 1
+        for (int j = 0; j < R; ++j) {  // occluded_filtered<R> reads slots 0..R-1
+            f3 W = mk3(0.f, 0.f, 0.f), nv = mk3(0.f, 0.f, 0.f), vn = mk3(0.f, 0.f, 0.f);
+            bool occj = true;
+            if (j < kr) {
+                const float4 Lp = h.light_p[l];
+                const float4 Ls = h.light_s[l];
+                const int nr = rays_of_light(fr, Ls);
+                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
+                                                                   : xyz(Lp);
+                // V = X - p (p as hi + lo), W = V / |V|^2
+                const f3 V = sub(sub(X, p), p_lo);
+                W = scl(V, __frcp_rn(dot(V, V)));
+                nv = scl(V, -1.0f);
+                // the plane first: a root u = num / (V.n) in (0, 1)
+                const float den = -dot(nv, pn);
+                occj = plane && den != 0.0f && num != 0.0f && ((num > 0.0f) == (den > 0.0f)) &&
+                       fabsf(num) < fabsf(den);
+                if (!occj) {
+                    const float S = dot(nv, nv);
+                    ok = ok && S >= 0x1p-60f && S <= 0x1p100f;
+                    vn = scl(nv, -__frsqrt_rn(S));
+                }
+                if (++s == nr) {
+                    s = 0;
+                    const uint32_t rest = lit & ~((2u << l) - 1u);
+                    l = rest ? __ffs(rest) - 1 : 0;
+                }
+            }
+            blocked |= occj ? (1u << j) : 0u;
+            vh[3 * j] = vn.x;
+            vh[3 * j + 1] = vn.y;
+            vh[3 * j + 2] = vn.z;
+            float* g = seg + 6 * j * kSegStride;
+            g[0] = W.x;
+            g[kSegStride] = W.y;
+            g[2 * kSegStride] = W.z;
+            g[3 * kSegStride] = nv.x;
+            g[4 * kSegStride] = nv.y;
+            g[5 * kSegStride] = nv.z;
+        }
+        const bool exact_only = !__all_sync(mask, ok);
+        if (R == 1) blocked = occluded_filtered<1>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
+        else if (R == 2) blocked = occluded_filtered<2>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
+        else if (R == 3) blocked = occluded_filtered<3>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
+        else blocked = occluded_filtered<4>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
+        // attribute the results to their lights in the same order
+#pragma unroll 1
+        for (int j = 0; j < kr; ++j) {
+            cnt += (blocked >> j) & 1u ? 0 : 1;
+            const float4 Lp = h.light_p[cl];
+            const int nr = rays_of_light(fr, h.light_s[cl]);
+            if (++cs == nr) {
+                const float vis = (float)cnt / (float)nr;
+                const f3 lh = normalize_rn(sub(sub(xyz(Lp), p), p_lo));
+                const float ndl = dot(n, lh);
+                const float sp = light_spec(fr, n, d, lh, ndl, e);
+                const float iv = Lp.w * vis;
+                out.A = fmaf(iv, ndl, out.A);
+                out.S = fmaf(iv * ks, sp, out.S);
+                if (HITREC) hr[hr_k + (size_t)(2 + cl) * hr_plane] = vis;
+                cs = 0;
+                cnt = 0;
+                const uint32_t rest = lit & ~((2u << cl) - 1u);
+                cl = rest ? __ffs(rest) - 1 : 0;
+            }
+        }
+        done += kr;
+    }
+    return out;
+}
+
 // ---------------------------------------------------------------- Section 3.8 sky
 // A ray that leaves the scene shows the sky panorama, looked up by the UV mapping
 // of its direction: u = 1/2 + atan2(d_z, d_x) / (2 pi), v = 1/2 - asin(d_y) / pi,
@@ -518,7 +773,13 @@ __device__ __forceinline__ void miss_add(const StagedScene& sc, f3 d, float T, f
 // reflection recursion of Section 3.7.1 unrolled forward: below the depth limit it
 // adds T((1 - rho) A c + S) and turns (o, o_lo, d, T) into the reflected ray with
 // T *= rho A; at the limit it adds T(A c + S).  HITREC: vis_l at hr[hr_k + ...].
-template <bool HITREC, bool CH, bool ACC>
+// FM (shading path of the staged brute-force kernels): 0 = the segment test alone
+// (shade_hit), 1 = the line filter (shade_hit_staged), 2 = chosen per scene by its
+// sphere count.  All give the same bits; the kernels that know the scene at launch
+// are compiled per path so that each carries only the code it runs.
+constexpr int kShadeAuto = 2;
+
+template <bool HITREC, bool CH, bool ACC, int FM = kShadeAuto>
 __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, int id,
                                            float t, f3& o, f3& o_lo, f3& d, float& T, float3& out,
                                            float* __restrict__ hr, size_t hr_k, size_t hr_plane) {
@@ -526,7 +787,15 @@ __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& f
     f3 po_lo;
     const f3 p = hg.p, n = hg.n, po = offset_origin(hg, fr.eps, po_lo);
     const float4 m = hg.m, m2 = hg.m2;
-    const HitShade sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+    HitShade sh;
+    // the line filter pays for its per-group set-up from kFilterMinPad spheres on
+    // (the same for every pixel of a launch, so only one of the paths runs hot)
+    bool filt = false;
+    if constexpr (!CH && !ACC) filt = FM == 1 || (FM == kShadeAuto && sc.hdr->ns_pad >= kFilterMinPad);
+    if (filt)
+        sh = shade_hit_staged<HITREC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+    else
+        sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
     const float A = sh.A, S = sh.S;
     if (k < fr.D) {
         const float w = T * (1.0f - m2.y) * A;
@@ -584,7 +853,7 @@ __device__ __forceinline__ bool queue_push(const PathQueue& q, uint32_t pix, f3 
 // shade_step.  HITREC: write (id, t, vis_l) per bounce, id = -1 after the path ends.
 // dq (first pass of rt_render_ws): a path whose bounce-1 ray hits is pushed to dq
 // instead of being shaded here; *deferred tells the caller not to store the pixel.
-template <bool HITREC, bool CH, bool ACC = false>
+template <bool HITREC, bool CH, bool ACC = false, int FM = kShadeAuto>
 __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame& fr, int x, int y,
                                               float* __restrict__ hr, size_t hr_plane, size_t hr_pix,
                                               const PathQueue* dq = nullptr, bool* deferred = nullptr) {
@@ -612,7 +881,7 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
             *deferred = true;
             return out;
         }
-        shade_step<HITREC, CH, ACC>(sc, fr, pix, k, id, t, o, o_lo, d, T, out, hr,
+        shade_step<HITREC, CH, ACC, FM>(sc, fr, pix, k, id, t, o, o_lo, d, T, out, hr,
                                     (size_t)k * (2 + h.nl) * hr_plane + hr_pix, hr_plane);
     }
     if (HITREC) {
@@ -667,14 +936,14 @@ __device__ __forceinline__ void store_pixel(const Frame& fr, int x, int y, bool 
 // Trace pixel (x, y) of the frame and store it (store_pixel's rules).  With dq, a
 // deferred pixel is not stored (F32) or stored with a placeholder that the pass
 // finishing its path overwrites (RGBA8, where four lanes share one store).
-template <bool HITREC, bool CH, bool ACC = false>
+template <bool HITREC, bool CH, bool ACC = false, int FM = kShadeAuto>
 __device__ __forceinline__ void render_pixel(const StagedScene& sc, const Frame& fr, int x, int y, bool valid,
                                              void* __restrict__ out, size_t pitch, float* __restrict__ hr,
                                              size_t hr_plane, const PathQueue* dq = nullptr) {
     float3 c = make_float3(0.f, 0.f, 0.f);
     bool deferred = false;
     if (valid)
-        c = trace_pixel<HITREC, CH, ACC>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x, dq,
+        c = trace_pixel<HITREC, CH, ACC, FM>(sc, fr, x, y, hr, hr_plane, (size_t)y * (size_t)fr.W + (size_t)x, dq,
                                          &deferred);
     store_pixel(fr, x, y, valid && !(deferred && fr.fmt == RT_OUT_F32), c, out, pitch);
 }
@@ -694,7 +963,7 @@ __device__ __forceinline__ void store_one(const Frame& fr, uint32_t pix, float3 
 // k, then (below the depth limit) trace the reflected ray; a hit is pushed to nq
 // (queue k + 1) or, when that is full, shaded here to its end.  A path that ends
 // here stores its pixel and its hit record's trailing -1 ids.
-template <bool HITREC>
+template <bool HITREC, int FM = kShadeAuto>
 __device__ __forceinline__ void trace_queued(const StagedScene& sc, const Frame& fr, const float4* __restrict__ e,
                                              int k, const PathQueue& nq, void* __restrict__ out, size_t pitch,
                                              float* __restrict__ hr, size_t hr_plane) {
@@ -709,7 +978,7 @@ __device__ __forceinline__ void trace_queued(const StagedScene& sc, const Frame&
     const size_t hr_pix = pix;
 #pragma unroll 1
     while (true) {
-        shade_step<HITREC, false, false>(sc, fr, pix, k, id, t, o, o_lo, d, T, c, hr,
+        shade_step<HITREC, false, false, FM>(sc, fr, pix, k, id, t, o, o_lo, d, T, c, hr,
                                          (size_t)k * (2 + h.nl) * hr_plane + hr_pix, hr_plane);
         if (k == fr.D) {
             k = fr.D + 1;
