@@ -508,6 +508,10 @@ def fwd_adjoint(dev, stream):
     ds.close()
     truth = S.perturbed_target(w)
     tgt = inverse.target_image(truth, w)
+    # untimed: the first optimizer step of a process imports PyTorch modules lazily
+    # (seconds on a cold box), which is not the loop's cost
+    inverse.inverse_render(w, tgt, steps=2, lr=0.05)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = inverse.inverse_render(w, tgt, steps=200, lr=0.05, truth=truth)
     torch.cuda.synchronize()

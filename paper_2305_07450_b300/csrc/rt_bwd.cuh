@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
         } else {
             // recompute: the forward trace itself, recording into registers/local memory
             float loc[kMaxBounce * (2 + RT_MAX_LIGHTS)];
-            trace_pixel<true, CH>(sc, fr, x, y, loc, 1, 0);
+            trace_pixel<true, CH, false, 0>(sc, fr, x, y, loc, 1, 0);  // recompute: the segment test alone
             for (int k = 0; k <= fr.D; ++k)
                 for (int f = 0; f < 2 + nl; ++f) rec[k * kRecStride + f] = loc[k * (2 + nl) + f];
         }
