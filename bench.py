@@ -346,16 +346,30 @@ def extras(args, dev, stream):
     """Secondary measurements (not the headline value): the forward render at
     1280x720 and 1920x1080 (64 spheres, 2 lights, depth 4), and the 64-scene
     batch as one graph-captured persistent launch against 64 per-frame launches."""
-    from paper_2305_07450_b300 import rt
+    import torch
+    from paper_2305_07450_b300 import autotune, rt
     out = {}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * 128 * 2 * 2032e6 / 1e12
     for name in ("720p", "1080p"):
         w = workload(name)
         ds = rt.DeviceScene(w.scene)
         o, pitch = rt.alloc_output(w.params, device=dev)
-        ms = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o, pitch=pitch, stream=stream), stream, 20)
-        out[name] = {"workload": w.name, "frames_per_s": 1e3 / ms, "ms_per_frame": ms}
+        launch = autotune.tune_render(ds, w.scene, w.camera, w.params, stream=stream)
+        wsb = rt.alloc_workspace(ds, w.params, device=dev) if launch.get("queued") else None
+        ms = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o, pitch=pitch, launch=launch,
+                                            stream=stream, workspace=wsb), stream, 20)
+        rec = {"workload": w.name, "frames_per_s": 1e3 / ms, "ms_per_frame": ms, "launch": launch}
+        if not args.no_cpu_baseline:
+            # algorithmic work from the oracle's counters on a bounded lattice sample
+            cs = oracle_sample(w, min(3.0, args.cpu_budget))
+            px = w.params.width * w.params.height
+            tf = flops_of(cs["per_pixel"]) * px / (ms / 1e3) / 1e12
+            rec.update({"mrays_per_s": rays_of(cs["per_pixel"]) * px / (ms / 1e3) / 1e6, "alg_tflops": tf,
+                        "frac_of_fp32_peak": tf / peak, "peak_tflops": peak,
+                        "work_sample": f"{cs['pixels']} pixels (lattice stride {cs['stride']})"})
+        out[name] = rec
         ds.close()
-    from paper_2305_07450_b300 import autotune
     ws = S.batch_scenes()
     dss = [rt.DeviceScene(w.scene) for w in ws]
     blaunch = autotune.tune_batch(dss, [w.scene for w in ws], [w.camera for w in ws], [w.params for w in ws],
