@@ -106,6 +106,8 @@ struct WsCtl {
     unsigned head[RT_MAX_DEPTH + 2];    // entries claimed from queue k
 };
 constexpr size_t kWsCtlBytes = 256;
+// Queue passes of at most this many paths per resident warp run in wide mode.
+constexpr unsigned kWidePathsPerWarp = 8;
 constexpr size_t kWsEntryBytes = 64;
 static_assert(sizeof(WsCtl) <= kWsCtlBytes, "workspace control block");
 
@@ -158,15 +160,20 @@ __global__ void __maxnreg__(80) rt_fwd_p0_kernel(const SceneView sv, const Frame
 
 // Pass k >= 1: persistent CTAs; each warp claims 32 entries of queue k at a time.
 // CTAs beyond the ones the queue's length needs return before staging.
+// A queue of at most wide_max paths (line-filter instances only) is taken one path
+// per warp (trace_queued_wide): such passes are bound by one warp's latency for one
+// hit, which spreading the hit's segments over the lanes cuts.
 template <bool HITREC, int FM>
 __global__ void __maxnreg__(80) rt_fwd_queue_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                     size_t pitch, float* __restrict__ hr, size_t hr_plane,
-                                                    int staging, unsigned char* __restrict__ ws, unsigned cap, int k) {
+                                                    int staging, unsigned char* __restrict__ ws, unsigned cap, int k,
+                                                    unsigned wide_max) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
     const unsigned n = min(*reinterpret_cast<volatile unsigned*>(&ctl->count[k]), cap);
-    const unsigned per_cta = 32u * blockDim.y;
+    const bool wide = FM == 1 && n <= wide_max;
+    const unsigned per_cta = wide ? blockDim.y : 32u * blockDim.y;
     if ((unsigned)blockIdx.x * per_cta >= n) return;  // the whole CTA, before any barrier
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if (staging == 1 && tid == 0) mbar_init(&bar, 1);
@@ -180,6 +187,20 @@ __global__ void __maxnreg__(80) rt_fwd_queue_kernel(const SceneView sv, const Fr
     sc.sky = sv.sky;
     const PathQueue cur = ws_queue(ws, cap, k);
     const PathQueue nxt = ws_queue(ws, cap, k + 1);
+    if constexpr (FM == 1) {
+        if (wide) {
+#pragma unroll 1
+            while (true) {
+                unsigned i = 0;
+                if (lane == 0) i = atomicAdd(&ctl->head[k], 1u);
+                i = __shfl_sync(0xffffffffu, i, 0);
+                if (i >= n) break;
+                trace_queued_wide<HITREC>(sc, fr, cur.ent + (size_t)i * 4, k, nxt, out, pitch, hr, hr_plane);
+                __syncwarp();
+            }
+            return;
+        }
+    }
 #pragma unroll 1
     while (true) {
         unsigned base = 0;
@@ -993,9 +1014,10 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         const unsigned gq =                                                                                       \
             std::min<unsigned>((unsigned)resident_ctas(rt_fwd_queue_kernel<HR, FM>, threads, smem),               \
                                std::max(1u, (cap + 32u * nwarps - 1) / (32u * nwarps)));                          \
+        const unsigned wide_max = gq * (unsigned)nwarps * kWidePathsPerWarp;                                     \
         for (int k = 1; k <= p->max_depth && cap > 0; ++k) {                                                      \
             rt_fwd_queue_kernel<HR, FM><<<gq, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr,   \
-                                                                  plane, hstage, w, cap, k);                      \
+                                                                  plane, hstage, w, cap, k, wide_max);            \
             g_launches++;                                                                                         \
         }                                                                                                         \
     } while (0)

@@ -773,6 +773,29 @@ __device__ __forceinline__ void miss_add(const StagedScene& sc, f3 d, float T, f
 // reflection recursion of Section 3.7.1 unrolled forward: below the depth limit it
 // adds T((1 - rho) A c + S) and turns (o, o_lo, d, T) into the reflected ray with
 // T *= rho A; at the limit it adds T(A c + S).  HITREC: vis_l at hr[hr_k + ...].
+// The colour and the next ray of bounce k from its shading (A, S): below the depth
+// limit T((1 - rho) A c + S) and the reflected ray with T *= rho A; at the limit
+// T(A c + S).
+__device__ __forceinline__ void step_tail(const Frame& fr, int k, float4 m, float4 m2, HitShade sh, f3 n, f3 po,
+                                          f3 po_lo, f3& o, f3& o_lo, f3& d, float& T, float3& out) {
+    const float A = sh.A, S = sh.S;
+    if (k < fr.D) {
+        const float w = T * (1.0f - m2.y) * A;
+        out.x = fmaf(w, m.x, fmaf(T, S, out.x));
+        out.y = fmaf(w, m.y, fmaf(T, S, out.y));
+        out.z = fmaf(w, m.z, fmaf(T, S, out.z));
+        T *= m2.y * A;
+        d = normalize_rn(fma3(n, -2.0f * dot(d, n), d));
+        o = po;
+        o_lo = po_lo;
+    } else {
+        const float w = T * A;
+        out.x = fmaf(w, m.x, fmaf(T, S, out.x));
+        out.y = fmaf(w, m.y, fmaf(T, S, out.y));
+        out.z = fmaf(w, m.z, fmaf(T, S, out.z));
+    }
+}
+
 // FM (shading path of the staged brute-force kernels): 0 = the segment test alone
 // (shade_hit), 1 = the line filter (shade_hit_staged), 2 = chosen per scene by its
 // sphere count.  All give the same bits; the kernels that know the scene at launch
@@ -796,22 +819,7 @@ __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& f
         sh = shade_hit_staged<HITREC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
     else
         sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
-    const float A = sh.A, S = sh.S;
-    if (k < fr.D) {
-        const float w = T * (1.0f - m2.y) * A;
-        out.x = fmaf(w, m.x, fmaf(T, S, out.x));
-        out.y = fmaf(w, m.y, fmaf(T, S, out.y));
-        out.z = fmaf(w, m.z, fmaf(T, S, out.z));
-        T *= m2.y * A;
-        d = normalize_rn(fma3(n, -2.0f * dot(d, n), d));
-        o = po;
-        o_lo = po_lo;
-    } else {
-        const float w = T * A;
-        out.x = fmaf(w, m.x, fmaf(T, S, out.x));
-        out.y = fmaf(w, m.y, fmaf(T, S, out.y));
-        out.z = fmaf(w, m.z, fmaf(T, S, out.z));
-    }
+    step_tail(fr, k, m, m2, sh, n, po, po_lo, o, o_lo, d, T, out);
 }
 
 // ---------------------------------------------------------------- bounce queues
@@ -1002,6 +1010,212 @@ __device__ __forceinline__ void trace_queued(const StagedScene& sc, const Frame&
             hr[(size_t)kk * (2 + h.nl) * hr_plane + hr_pix] = __int_as_float(-1);
     }
     store_one(fr, pix, c, out, pitch);
+}
+
+// ---------------------------------------------------------------- wide queue passes
+// When a queue pass holds few paths it is bound by the latency of one warp shading
+// one hit (a lane traces the hit's 19 shadow segments against every sphere, in
+// groups), not by work.  In wide mode a warp takes ONE path: lane j sets up and
+// tests segment j of the hit (the filtered loop with one segment per lane), the
+// visible counts per light come from warp votes, and the next ray's closest hit is
+// split by blocks of spheres across the lanes and reduced to the lowest (t, index).
+// Every per-segment and per-sphere value is computed by the same operations as in
+// the one-lane path, and the shading sums run over the lights in the same order,
+// so the results are bit-identical; only the latency changes.
+
+// Closest hit with the spheres split across the warp (all 32 lanes call): lane j
+// tests blocks j, j + 32, ...; the lexicographic minimum of (t, index) over the
+// lanes equals the strict-< scan in index order.  Then the plane, as closest_hit.
+__device__ __forceinline__ int closest_hit_wide(const StagedScene& sc, f3 o, f3 d, float& t_out) {
+    const int lane = threadIdx.x & 31;
+    float tb = __int_as_float(0x7f800000);
+    int best = -1;
+    const int n = sc.hdr->ns_pad;
+    const RayCross rp = ray_cross(o, d);
+#pragma unroll 1
+    for (int i0 = lane * kPad; i0 < n; i0 += 32 * kPad) closest_block(sc.geo + i0, i0, rp, tb, best);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float t2 = __shfl_xor_sync(0xffffffffu, tb, off);
+        const int b2 = __shfl_xor_sync(0xffffffffu, best, off);
+        if (b2 >= 0 && (best < 0 || t2 < tb || (t2 == tb && b2 < best))) {
+            tb = t2;
+            best = b2;
+        }
+    }
+    const SceneHdr& h = *sc.hdr;
+    if (h.has_plane) {
+        const f3 pn = xyz(h.plane_g);
+        const float den = dot(d, pn);
+        if (den != 0.0f) {
+            const float t = __fdiv_rn(-(dot(o, pn) + h.plane_g.w), den);
+            if (t > 0.0f && t < tb) {
+                tb = t;
+                best = h.ns;
+            }
+        }
+    }
+    t_out = tb;
+    return best;
+}
+
+// shade_hit_staged with the hit's segments spread over the warp (all 32 lanes call
+// with the same hit; the result is the same in every lane).
+template <bool HITREC>
+__device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const Frame& fr, uint32_t pix, int k,
+                                                   f3 p, f3 p_lo, f3 n, f3 po, f3 d, float ks, float e,
+                                                   float* __restrict__ hr, size_t hr_k, size_t hr_plane) {
+    const SceneHdr& h = *sc.hdr;
+    const int lane = threadIdx.x & 31;
+    HitShade out{fr.ka, 0.0f};
+    uint32_t lit = 0;
+    int total = 0;
+#pragma unroll 1
+    for (int li = 0; li < h.nl; ++li) {
+        const f3 lh = normalize_rn(sub(sub(xyz(h.light_p[li]), p), p_lo));
+        if (dot(n, lh) > 0.0f) {
+            lit |= 1u << li;
+            total += rays_of_light(fr, h.light_s[li]);
+        }
+        if (HITREC && lane == 0) hr[hr_k + (size_t)(2 + li) * hr_plane] = 0.0f;
+    }
+    int cnt[RT_MAX_LIGHTS];
+#pragma unroll
+    for (int li = 0; li < RT_MAX_LIGHTS; ++li) cnt[li] = 0;
+    float* seg = s_seg + (threadIdx.x + blockDim.x * threadIdx.y);
+    const bool plane = h.has_plane != 0;
+    const f3 pn = xyz(h.plane_g);
+    const float num = -(dot(po, pn) + h.plane_g.w);
+#pragma unroll 1
+    for (int c0 = 0; c0 < total; c0 += 32) {
+        // segment c0 + lane: its light l and sample s, in the one-lane path's order
+        int rem = c0 + lane, l = -1;
+        const bool valid = rem < total;
+        if (valid) {
+            uint32_t rest = lit;
+            while (true) {
+                l = __ffs(rest) - 1;
+                const int nr = rays_of_light(fr, h.light_s[l]);
+                if (rem < nr) break;
+                rem -= nr;
+                rest &= rest - 1u;
+            }
+        }
+        f3 W = mk3(0.f, 0.f, 0.f), nv = mk3(0.f, 0.f, 0.f), vn = mk3(0.f, 0.f, 0.f);
+        bool occj = true, ok = true;
+        if (valid) {
+            const int s = rem;
+            const float4 Lp = h.light_p[l];
+            const float4 Ls = h.light_s[l];
+            const int nr = rays_of_light(fr, Ls);
+            // sample s of an area light uses the words of Philox call s / 2
+            uint4 w = make_uint4(0, 0, 0, 0);
+            if (Ls.x > 0.0f && (s & 1))
+                w = philox10(make_uint4(pix, (uint32_t)k, (uint32_t)l, (uint32_t)(s >> 1)), fr.key0, fr.key1);
+            const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
+                                                               : xyz(Lp);
+            const f3 V = sub(sub(X, p), p_lo);
+            W = scl(V, __frcp_rn(dot(V, V)));
+            nv = scl(V, -1.0f);
+            const float den = -dot(nv, pn);
+            occj = plane && den != 0.0f && num != 0.0f && ((num > 0.0f) == (den > 0.0f)) && fabsf(num) < fabsf(den);
+            if (!occj) {
+                const float S = dot(nv, nv);
+                ok = S >= 0x1p-60f && S <= 0x1p100f;
+                vn = scl(nv, -__frsqrt_rn(S));
+            }
+        }
+        float vh[3 * kShadowGroup];
+        vh[0] = vn.x;
+        vh[1] = vn.y;
+        vh[2] = vn.z;
+        seg[0] = W.x;
+        seg[kSegStride] = W.y;
+        seg[2 * kSegStride] = W.z;
+        seg[3 * kSegStride] = nv.x;
+        seg[4 * kSegStride] = nv.y;
+        seg[5 * kSegStride] = nv.z;
+        const bool exact_only = !__all_sync(0xffffffffu, ok);
+        const uint32_t blocked = occluded_filtered<1>(sc.geo, h.ns_pad, 0xffffffffu, po, vh, occj ? 1u : 0u, seg,
+                                                      exact_only);
+        const bool vis = valid && !(blocked & 1u);
+#pragma unroll
+        for (int li = 0; li < RT_MAX_LIGHTS; ++li)
+            if ((lit >> li) & 1u) cnt[li] += __popc(__ballot_sync(0xffffffffu, vis && l == li));
+    }
+    // the shading sums in light order, as the one-lane attribution
+#pragma unroll
+    for (int li = 0; li < RT_MAX_LIGHTS; ++li) {
+        if ((lit >> li) & 1u) {
+            const float4 Lp = h.light_p[li];
+            const int nr = rays_of_light(fr, h.light_s[li]);
+            const float vis = (float)cnt[li] / (float)nr;
+            const f3 lh = normalize_rn(sub(sub(xyz(Lp), p), p_lo));
+            const float ndl = dot(n, lh);
+            const float sp = light_spec(fr, n, d, lh, ndl, e);
+            const float iv = Lp.w * vis;
+            out.A = fmaf(iv, ndl, out.A);
+            out.S = fmaf(iv * ks, sp, out.S);
+            if (HITREC && lane == 0) hr[hr_k + (size_t)(2 + li) * hr_plane] = vis;
+        }
+    }
+    return out;
+}
+
+// trace_queued in wide mode: the whole warp carries the path of entry e (all 32
+// lanes call with the same entry); lane 0 pushes, stores and writes the record.
+template <bool HITREC>
+__device__ __forceinline__ void trace_queued_wide(const StagedScene& sc, const Frame& fr,
+                                                  const float4* __restrict__ e, int k, const PathQueue& nq,
+                                                  void* __restrict__ out, size_t pitch, float* __restrict__ hr,
+                                                  size_t hr_plane) {
+    const SceneHdr& h = *sc.hdr;
+    const int lane = threadIdx.x & 31;
+    const int kq = k + 1;
+    const float4 e0 = e[0], e1 = e[1], e2 = e[2], e3 = e[3];
+    f3 o = mk3(e0.x, e0.y, e0.z), o_lo = mk3(e1.x, e1.y, e1.z), d = mk3(e2.x, e2.y, e2.z);
+    float T = e0.w, t = e2.w;
+    float3 c = make_float3(e3.x, e3.y, e3.z);
+    int id = __float_as_int(e3.w);
+    const uint32_t pix = __float_as_uint(e1.w);
+    const size_t hr_pix = pix;
+#pragma unroll 1
+    while (true) {
+        const size_t hr_k = (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
+        const HitGeom hg = hit_geometry<false>(sc, id, o, o_lo, d, t, fr.refl_inv_max);
+        f3 po_lo;
+        const f3 po = offset_origin(hg, fr.eps, po_lo);
+        const HitShade sh =
+            shade_hit_wide<HITREC>(sc, fr, pix, k, hg.p, hg.p_lo, hg.n, po, d, hg.m.w, hg.m2.x, hr, hr_k, hr_plane);
+        step_tail(fr, k, hg.m, hg.m2, sh, hg.n, po, po_lo, o, o_lo, d, T, c);
+        if (k == fr.D) {
+            k = fr.D + 1;
+            break;
+        }
+        ++k;
+        id = closest_hit_wide(sc, o, d, t);
+        if (HITREC && lane == 0) {
+            float* rec = hr + (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
+            rec[0] = __int_as_float(id);
+            rec[hr_plane] = t;
+        }
+        if (id < 0) {
+            miss_add(sc, d, T, c);
+            break;
+        }
+        if (k == kq) {
+            bool pushed = false;
+            if (lane == 0) pushed = queue_push(nq, pix, o, o_lo, d, T, c, id, t);
+            if (__shfl_sync(0xffffffffu, pushed, 0)) return;
+        }
+    }
+    if (lane == 0) {
+        if (HITREC) {
+            for (int kk = k + 1; kk <= fr.D; ++kk)
+                hr[(size_t)kk * (2 + h.nl) * hr_plane + hr_pix] = __int_as_float(-1);
+        }
+        store_one(fr, pix, c, out, pitch);
+    }
 }
 
 }  // namespace rtd

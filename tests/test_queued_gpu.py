@@ -139,3 +139,12 @@ def test_256_workload_against_oracle():
     ref, margin, sens = oracle_reference(w)
     ok, st = compare_f32(img[..., :3].reshape(-1, 3), ref, margin, sens, w.scene.scene_scale)
     assert st["failing"] == 0 and st["frac_within_1e-4"] >= 0.99, st
+
+
+@pytest.mark.parametrize("entries", [None, 0, 37])
+def test_deep_mirror_paths_with_the_line_filter(entries):
+    """160 mirror spheres (the line-filter kernels; short queues run one path per
+    warp): every pixel and hit-record entry equal to the one-pass kernel's."""
+    w = mirror_scene(n=160, seed=12)
+    assert_same(w, hitrec=True, ws_bytes=None if entries is None else 256 + 128 * entries)
+    assert_same(w, fmt=S.OUT_RGBA8)
