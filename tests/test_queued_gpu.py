@@ -148,3 +148,28 @@ def test_deep_mirror_paths_with_the_line_filter(entries):
     w = mirror_scene(n=160, seed=12)
     assert_same(w, hitrec=True, ws_bytes=None if entries is None else 256 + 128 * entries)
     assert_same(w, fmt=S.OUT_RGBA8)
+
+
+def test_maxima_in_wide_passes():
+    """16 lights (point, square-area and spherical), 1024 samples per sampled light,
+    bounce limit 16, and 128 filler spheres below the plane so that the line-filter
+    kernels run: every queue of this small frame is short, so every pass after the
+    first takes one path per warp (over 4 000 segments a hit, in chunks of 32 lanes);
+    pixels and hit records equal to the one-pass kernel's."""
+    from oracle_pins import light, mk, plane_rec, sphere
+    rng = np.random.default_rng(16)
+    sph = [sphere((0.0, 1.0, 6.0), 3.0, albedo=(0.2, 0.3, 0.9), refl=0.95),
+           sphere((0.0, 1.0, -6.0), 3.0, albedo=(0.9, 0.3, 0.2), refl=0.95),
+           sphere((-1.2, 0.6, 1.5), 0.5, albedo=(0.3, 0.9, 0.3), refl=0.5),
+           sphere((1.3, 1.8, 1.0), 0.4, albedo=(0.9, 0.9, 0.2), refl=0.5)]
+    sph += [sphere((float(x), -20.0, float(z)), 0.3) for x in range(-8, 8) for z in range(8)]
+    lig = [light((float(rng.uniform(-6, 6)), float(rng.uniform(8, 10)), float(rng.uniform(-3, 3))),
+                 float(rng.uniform(0.05, 0.1))) for _ in range(12)]
+    lig += [light((-2.0, 9.5, -1.0), 0.2, area=1.0), light((2.5, 9.0, 1.5), 0.2, area=0.7)]
+    lig += [light((0.0, 10.0, 0.5), 0.2, srad=0.4), light((-3.0, 9.0, 2.0), 0.2, srad=0.3)]
+    sc, cam, p = mk(spheres=sph, plane=plane_rec(refl=0.6), lights=lig, camera=(0, 1, 0, 0, 0, 50),
+                    W=20, H=14, D=16, samples=1024, seed=99)
+    p.eps = 5e-4
+    p.out_format = S.OUT_F32
+    assert sc.n_spheres >= 128
+    assert_same(S.Workload("max_wide", sc, cam, p), hitrec=True)
