@@ -11,6 +11,7 @@
 #include <mutex>
 #include <numeric>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/rt.h"
@@ -63,6 +64,15 @@ static SceneView view_of(const rt_scene* s) {
 }
 
 // ============================================================ forward kernel
+// Register budget of the queued render's kernels per shading path: 80 for the
+// segment test alone (6 CTAs of 128 threads per SM), 128 for the line filter, whose
+// out-of-line group loop saves the caller's state per call (4 CTAs per SM; 4K
+// queued frame 9.97 ms against 10.22 at 80, 10.11 at 96, 10.48 at 104, 10.25 at
+// 112, 10.46 at 144, 10.39 at 168).  The one-pass kernel keeps 80 in both paths
+// (its line-filter instance: 4K 11.89 ms at 80 against 12.52 at 128).
+constexpr int fwd_regs(int fm) { return fm == 1 ? 128 : 80; }
+
+
 // One thread per pixel.  The CTA covers block_x x block_y pixels; warp w covers an
 // 8 x 4 patch (lanes 0..7 = one row), so that a warp's primary and shadow rays
 // are coherent.  The scene header and geometry table are staged in shared memory
@@ -124,7 +134,7 @@ __device__ __forceinline__ PathQueue ws_queue(unsigned char* ws, unsigned cap, i
 // warp claims 8 x 4 pixel patches (in the order of block_x x block_y tiles) and
 // traces them, pushing paths whose bounce-1 ray hits to queue 1.
 template <bool HITREC, int FM>
-__global__ void __maxnreg__(80) rt_fwd_p0_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
+__global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_p0_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                  size_t pitch, float* __restrict__ hr, size_t hr_plane, int staging,
                                                  int block_x, int block_y, int tiles_x, unsigned n_items,
                                                  unsigned char* __restrict__ ws, unsigned cap) {
@@ -164,7 +174,7 @@ __global__ void __maxnreg__(80) rt_fwd_p0_kernel(const SceneView sv, const Frame
 // per warp (trace_queued_wide): such passes are bound by one warp's latency for one
 // hit, which spreading the hit's segments over the lanes cuts.
 template <bool HITREC, int FM>
-__global__ void __maxnreg__(80) rt_fwd_queue_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
+__global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                     size_t pitch, float* __restrict__ hr, size_t hr_plane,
                                                     int staging, unsigned char* __restrict__ ws, unsigned cap, int k,
                                                     unsigned wide_max) {
@@ -574,10 +584,30 @@ int resident_ctas(K kernel, int threads, size_t smem) {
 
 template <typename K>
 rt_status ensure_smem(K kernel, size_t bytes) {
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return RT_ERR_CUDA;
-    if (bytes + fa.sharedSizeBytes <= 48 * 1024) return RT_OK;
-    const int cap = max_smem_optin() - (int)fa.sharedSizeBytes;  // what the kernel's static shared memory leaves
+    // the kernel's static shared memory, looked up once per kernel (the query costs
+    // tens of microseconds, as much as a small frame)
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, size_t>> known;
+    size_t stat = 0;
+    bool found = false;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (const auto& e : known)
+            if (e.first == (const void*)kernel) {
+                stat = e.second;
+                found = true;
+                break;
+            }
+    }
+    if (!found) {
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return RT_ERR_CUDA;
+        stat = fa.sharedSizeBytes;
+        std::lock_guard<std::mutex> g(mu);
+        known.emplace_back((const void*)kernel, stat);
+    }
+    if (bytes + stat <= 48 * 1024) return RT_OK;
+    const int cap = max_smem_optin() - (int)stat;  // what the kernel's static shared memory leaves
     if ((long long)bytes > cap) return RT_ERR_UNSUPPORTED;
     return cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
 }
