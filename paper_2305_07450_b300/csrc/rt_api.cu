@@ -64,12 +64,13 @@ static SceneView view_of(const rt_scene* s) {
 }
 
 // ============================================================ forward kernel
-// Register budget of the queued render's kernels per shading path: 80 for the
-// segment test alone (6 CTAs of 128 threads per SM), 128 for the line filter, whose
-// out-of-line group loop saves the caller's state per call (4 CTAs per SM; 4K
-// queued frame 9.97 ms against 10.22 at 80, 10.11 at 96, 10.48 at 104, 10.25 at
-// 112, 10.46 at 144, 10.39 at 168).  The one-pass kernel keeps 80 in both paths
-// (its line-filter instance: 4K 11.89 ms at 80 against 12.52 at 128).
+// Register budget of the forward kernels per shading path: 80 for the segment test
+// alone (6 CTAs of 128 threads per SM), 128 for the line filter, whose out-of-line
+// group loop saves the caller's state per call and whose groups of 7 segments hold
+// 42 registers of unit vectors (4 CTAs per SM; 4K queued frame with groups of 4:
+// 9.97 ms against 10.22 at 80, 10.11 at 96, 10.48 at 104, 10.25 at 112, 10.46 at
+// 144, 10.39 at 168; with groups of 7 the one-pass kernel too: 11.73 ms at 128
+// against 12.05 ms for groups of 4 at 80).
 constexpr int fwd_regs(int fm) { return fm == 1 ? 128 : 80; }
 
 
@@ -80,7 +81,7 @@ constexpr int fwd_regs(int fm) { return fm == 1 ? 128 : 80; }
 // B300 at 4K as 16.05 ms against 16.25 (96), 16.01 (72), 16.02 (64) and slower
 // at 104 / 112 / 128; the spills it causes sit outside the sphere loops.
 template <bool HITREC, bool CH, int FM>
-__global__ void __maxnreg__(80) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
+__global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                      size_t pitch, float* __restrict__ hr, size_t hr_plane,
                                                      int staging, int block_x, int block_y) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -549,15 +550,15 @@ int max_smem_optin() {
 
 // The whole geometry table is staged unless it does not fit (or the tiled loop is
 // forced with staging = 3).
-constexpr size_t kStaticSmemReserve = 28 * 1024;
+constexpr size_t kStaticSmemReserve = 4 * 1024 + 6 * 4 * kSegStride * kFiltGroup;
 size_t stage_smem_bytes(bool chunked, int ns_pad, int nwarps) {
     return chunked ? sizeof(SceneHdr) + (size_t)nwarps * kChunk * 16 : sizeof(SceneHdr) + (size_t)ns_pad * 16;
 }
 
 bool use_tiled_loop(const Launch& L, int ns_pad) {
     if (L.staging == 3) return true;
-    // room left for the kernels' static shared memory (the shadow test's 24 KB of
-    // segment vectors and the barriers)
+    // room left for the kernels' static shared memory (the shadow test's segment
+    // vectors, 42 KB, and the barriers)
     return stage_smem_bytes(false, ns_pad, 0) + kStaticSmemReserve > (size_t)max_smem_optin();
 }
 

@@ -98,9 +98,9 @@ __global__ void __launch_bounds__(128, 6) rt_batch_kernel(unsigned char* __restr
         const int y = ty * block_y + (warp / wpr) * 4 + (lane >> 3);
         const bool valid = x < s_fr.W && y < s_fr.H;
         // segment test alone: the batch's point-light scenes trace one group of at most
-        // four segments per hit, where the line filter's set-up and its 24 KB of shared
-        // memory cost more than they save (64-scene batch on B300: 12.81 ms against
-        // 14.58 ms with the filter); the bits are the same either way
+        // four segments per hit, where the line filter's set-up and its shared memory
+        // cost more than they save (64-scene batch on B300: 12.81 ms against 14.58 ms
+        // with the filter in groups of 4); the bits are the same either way
         render_pixel<false, CH, false, 0>(sc, s_fr, x, y, valid, s_out, s_pitch, nullptr, 0);
         __syncthreads();  // every thread is done with this tile, its slot and the staged scene
         buf ^= 1;
