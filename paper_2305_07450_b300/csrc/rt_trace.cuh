@@ -415,6 +415,20 @@ __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, cons
 }
 
 // ---------------------------------------------------------------- Section 3.6.1
+// The in-plane axes of a spherical light seen from p: w = normalize(p - L), u =
+// normalize(w x up), v = u x w (up = +y, or +x when w is nearly vertical).  They
+// depend on the hit and the light only, so a hit computes them once per light.
+struct LightFrame {
+    f3 u, v;
+};
+__device__ __forceinline__ LightFrame light_frame(f3 p, float4 Lp) {
+    const f3 wv = normalize_rn(sub(p, xyz(Lp)));
+    const f3 up = fabsf(wv.y) < 0.999f ? mk3(0.f, 1.f, 0.f) : mk3(1.f, 0.f, 0.f);
+    const f3 u = normalize_rn(mk3(wv.y * up.z - wv.z * up.y, wv.z * up.x - wv.x * up.z, wv.x * up.y - wv.y * up.x));
+    const f3 v = mk3(u.y * wv.z - u.z * wv.y, u.z * wv.x - u.x * wv.z, u.x * wv.y - u.y * wv.x);
+    return LightFrame{u, v};
+}
+
 // Target point of shadow ray s of sampled light (Lp, Ls) seen from p.
 // Square area light of side a: n = g*g strata, sample s in stratum
 // (s mod g, s div g) at ((i + xi1)/g - 1/2, (j + xi2)/g - 1/2) * a in x and z,
@@ -423,8 +437,9 @@ __device__ __forceinline__ void occluded_group(const StagedScene& sc, f3 o, cons
 // Spherical light of radius R: sunflower point s of n on the great circle facing p,
 // radius R sqrt(s/n) at angle s * phi, phi = pi (3 - sqrt 5) (the angle is reduced
 // exactly as 2 pi frac(s (3 - sqrt 5) / 2) in 32-bit fixed point).
-__device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k, int l, int s, f3 p,
-                                           float4 Lp, float4 Ls, uint4& w) {
+// lf: light_frame(p, Lp) for a spherical light (unused otherwise).
+__device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k, int l, int s, float4 Lp, float4 Ls,
+                                           uint4& w, const LightFrame& lf) {
     if (Ls.x > 0.0f) {
         if ((s & 1) == 0)
             w = philox10(make_uint4(pix, (uint32_t)k, (uint32_t)l, (uint32_t)(s >> 1)), fr.key0, fr.key1);
@@ -435,15 +450,11 @@ __device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k,
         const float a = Ls.x, ginv = fr.sample_g_inv;
         return mk3(Lp.x + (((float)i + xi1) * ginv - 0.5f) * a, Lp.y, Lp.z + (((float)j + xi2) * ginv - 0.5f) * a);
     }
-    const f3 wv = normalize_rn(sub(p, xyz(Lp)));
-    const f3 up = fabsf(wv.y) < 0.999f ? mk3(0.f, 1.f, 0.f) : mk3(1.f, 0.f, 0.f);
-    const f3 u = normalize_rn(mk3(wv.y * up.z - wv.z * up.y, wv.z * up.x - wv.x * up.z, wv.x * up.y - wv.y * up.x));
-    const f3 v = mk3(u.y * wv.z - u.z * wv.y, u.z * wv.x - u.x * wv.z, u.x * wv.y - u.y * wv.x);
     const float r = Ls.y * sqrtf((float)s / (float)fr.nsamp);
     const uint32_t frac = (uint32_t)s * 0x61C88647u;  // 2^32 (3 - sqrt 5) / 2
     float sn, cs;
     sincospif((float)(frac >> 8) * (1.0f / 8388608.0f), &sn, &cs);  // 2 frac
-    return add(xyz(Lp), add(scl(u, r * cs), scl(v, r * sn)));
+    return add(xyz(Lp), add(scl(lf.u, r * cs), scl(lf.v, r * sn)));
 }
 
 // ---------------------------------------------------------------- Sections 3.5-3.6
@@ -503,6 +514,8 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
         f3 sw[kShadowGroup], snv[kShadowGroup];  // W and -V of each segment
         bool occ[kShadowGroup];
         int l = cl, s = cs;
+        LightFrame lf{};  // of spherical light lf_l
+        int lf_l = -1;
 #pragma unroll
         for (int j = 0; j < kShadowGroup; ++j) {
             sw[j] = mk3(0.f, 0.f, 0.f);
@@ -512,7 +525,11 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
                 const float4 Lp = h.light_p[l];
                 const float4 Ls = h.light_s[l];
                 const int nr = rays_of_light(fr, Ls);
-                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
+                if (Ls.y > 0.0f && lf_l != l) {
+                    lf = light_frame(p, Lp);
+                    lf_l = l;
+                }
+                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf)
                                                                    : xyz(Lp);
                 // V = X - p (p as hi + lo), W = V / |V|^2
                 const f3 V = sub(sub(X, p), p_lo);
@@ -589,6 +606,8 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
     int cl = lit ? __ffs(lit) - 1 : 0, cs = 0, cnt = 0;
     int l = cl, s = 0;
     uint4 w = make_uint4(0, 0, 0, 0);
+    LightFrame lf{};  // of spherical light lf_l
+    int lf_l = -1;
     int done = 0;
     const unsigned mask = __activemask();
     float* seg = s_seg + (threadIdx.x + blockDim.x * threadIdx.y);
@@ -611,7 +630,11 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 const float4 Lp = h.light_p[l];
                 const float4 Ls = h.light_s[l];
                 const int nr = rays_of_light(fr, Ls);
-                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
+                if (Ls.y > 0.0f && lf_l != l) {
+                    lf = light_frame(p, Lp);
+                    lf_l = l;
+                }
+                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf)
                                                                    : xyz(Lp);
                 // V = X - p (p as hi + lo), W = V / |V|^2
                 const f3 V = sub(sub(X, p), p_lo);
@@ -1123,7 +1146,8 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
             uint4 w = make_uint4(0, 0, 0, 0);
             if (Ls.x > 0.0f && (s & 1))
                 w = philox10(make_uint4(pix, (uint32_t)k, (uint32_t)l, (uint32_t)(s >> 1)), fr.key0, fr.key1);
-            const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, p, Lp, Ls, w)
+            const LightFrame lf = Ls.y > 0.0f ? light_frame(p, Lp) : LightFrame{};
+            const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf)
                                                                : xyz(Lp);
             const f3 V = sub(sub(X, p), p_lo);
             W = scl(V, __frcp_rn(dot(V, V)));
