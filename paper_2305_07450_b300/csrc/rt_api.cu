@@ -83,7 +83,8 @@ constexpr int fwd_regs(int fm) { return fm == 1 ? 128 : 80; }
 template <bool HITREC, bool CH, int FM>
 __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                      size_t pitch, float* __restrict__ hr, size_t hr_plane,
-                                                     int staging, int block_x, int block_y) {
+                                                     int staging, int block_x, int block_y, uint32_t flower_off,
+                                                     int flower_n) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -99,6 +100,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_kernel(const SceneView sv, cons
     float4* tab = reinterpret_cast<float4*>(smem + sizeof(SceneHdr));
     StagedScene sc{hdr, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)warp * kChunk : nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
+    sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
 
     const int wpr = block_x >> 3;
     const int x = fr.rx0 + blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
@@ -138,7 +140,8 @@ template <bool HITREC, int FM>
 __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_p0_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                  size_t pitch, float* __restrict__ hr, size_t hr_plane, int staging,
                                                  int block_x, int block_y, int tiles_x, unsigned n_items,
-                                                 unsigned char* __restrict__ ws, unsigned cap) {
+                                                 unsigned char* __restrict__ ws, unsigned cap, uint32_t flower_off,
+                                                 int flower_n) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -151,6 +154,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_p0_kernel(const SceneView sv, c
     const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
+    sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
     WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
     const PathQueue q1 = ws_queue(ws, cap, 1);
     const int wpr = block_x >> 3, wpt = (block_x * block_y) >> 5;
@@ -178,7 +182,7 @@ template <bool HITREC, int FM>
 __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                     size_t pitch, float* __restrict__ hr, size_t hr_plane,
                                                     int staging, unsigned char* __restrict__ ws, unsigned cap, int k,
-                                                    unsigned wide_max) {
+                                                    unsigned wide_max, uint32_t flower_off, int flower_n) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
@@ -196,6 +200,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv
     const SceneHdr* hdr = reinterpret_cast<const SceneHdr*>(smem);
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
+    sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
     const PathQueue cur = ws_queue(ws, cap, k);
     const PathQueue nxt = ws_queue(ws, cap, k + 1);
     if constexpr (FM == 1) {
@@ -555,11 +560,11 @@ size_t stage_smem_bytes(bool chunked, int ns_pad, int nwarps) {
     return chunked ? sizeof(SceneHdr) + (size_t)nwarps * kChunk * 16 : sizeof(SceneHdr) + (size_t)ns_pad * 16;
 }
 
-bool use_tiled_loop(const Launch& L, int ns_pad) {
+bool use_tiled_loop(const Launch& L, int ns_pad, size_t extra = 0) {
     if (L.staging == 3) return true;
     // room left for the kernels' static shared memory (the shadow test's segment
     // vectors, 42 KB, and the barriers)
-    return stage_smem_bytes(false, ns_pad, 0) + kStaticSmemReserve > (size_t)max_smem_optin();
+    return stage_smem_bytes(false, ns_pad, 0) + 16 + extra + kStaticSmemReserve > (size_t)max_smem_optin();
 }
 
 // Resident CTAs of `kernel` on the current device (threads per CTA, dynamic shared
@@ -1022,8 +1027,11 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         g_launches++;
         return cuda_status(cudaGetLastError());
     }
-    const bool chunked = use_tiled_loop(L, s->ns_pad);
-    const size_t smem = stage_smem_bytes(chunked, s->ns_pad, nwarps);
+    // the sunflower table of a spherical light's samples follows the staged data
+    const int flower_n = s->any_sphere_light ? p->shadow_samples : 0;
+    const bool chunked = use_tiled_loop(L, s->ns_pad, (size_t)flower_n * 16);
+    const uint32_t flower_off = (uint32_t)((stage_smem_bytes(chunked, s->ns_pad, nwarps) + 15) / 16 * 16);
+    const size_t smem = flower_off + (size_t)flower_n * 16;
     if (ws && !chunked) {
         // queued render: reset the counters, first pass, then one pass per bounce
         unsigned char* w = static_cast<unsigned char*>(ws);
@@ -1040,7 +1048,8 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         const unsigned g0 = std::min<unsigned>((unsigned)resident_ctas(rt_fwd_p0_kernel<HR, FM>, threads, smem), \
                                                (n_items + nwarps - 1) / nwarps);                                  \
         rt_fwd_p0_kernel<HR, FM><<<g0, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr, plane,   \
-                                                           hstage, L.bx, L.by, (int)grid.x, n_items, w, cap);     \
+                                                           hstage, L.bx, L.by, (int)grid.x, n_items, w, cap,      \
+                                                           flower_off, flower_n);                                 \
         g_launches++;                                                                                             \
         const unsigned gq =                                                                                       \
             std::min<unsigned>((unsigned)resident_ctas(rt_fwd_queue_kernel<HR, FM>, threads, smem),               \
@@ -1048,7 +1057,8 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         const unsigned wide_max = gq * (unsigned)nwarps * kWidePathsPerWarp;                                     \
         for (int k = 1; k <= p->max_depth && cap > 0; ++k) {                                                      \
             rt_fwd_queue_kernel<HR, FM><<<gq, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr,   \
-                                                                  plane, hstage, w, cap, k, wide_max);            \
+                                                                  plane, hstage, w, cap, k, wide_max, flower_off, \
+                                                                  flower_n);                                      \
             g_launches++;                                                                                         \
         }                                                                                                         \
     } while (0)
@@ -1066,7 +1076,7 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
     do {                                                                                                         \
         if ((st = ensure_smem(rt_fwd_kernel<HR, CHK, FM>, smem)) != RT_OK) return st;                           \
         rt_fwd_kernel<HR, CHK, FM><<<grid, block, smem, st_>>>(view_of(s), fr, out_dev, out_pitch_bytes, hr,    \
-                                                              plane, hstage, L.bx, L.by);                       \
+                                                              plane, hstage, L.bx, L.by, flower_off, flower_n); \
     } while (0)
     // the shading path compiled in: the line filter from kFilterMinPad spheres on
     // (the tiled loop keeps the segment test)

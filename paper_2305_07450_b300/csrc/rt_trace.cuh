@@ -24,7 +24,27 @@ struct StagedScene {
     const float4* mat2;    // global
     BvhView bvh;           // hierarchy over the spheres (ACC kernels only)
     SkyView sky;           // panorama of the misses (null: black)
+    const float4* flower;  // shared sunflower table (sunflower_table), or null: computed per sample
 };
+
+// The sunflower points of a spherical light that do not depend on the hit: for
+// sample s of n, (sqrt(s / n), cos 2 pi f_s, sin 2 pi f_s) with f_s = frac(s (3 -
+// sqrt 5) / 2) -- the values sample_point otherwise computes per sample, by the same
+// operations.  Written into shared memory at `tab` by all threads of the CTA (which
+// must all call), for s < n_tab; returns the table (null when n_tab is 0).
+__device__ __forceinline__ const float4* sunflower_table(float4* tab, int n_tab, int nsamp) {
+    if (n_tab <= 0) return nullptr;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nth = blockDim.x * blockDim.y;
+    for (int s = tid; s < n_tab; s += nth) {
+        const float q = sqrtf((float)s / (float)nsamp);
+        const uint32_t frac = (uint32_t)s * 0x61C88647u;  // 2^32 (3 - sqrt 5) / 2
+        float sn, cs;
+        sincospif((float)(frac >> 8) * (1.0f / 8388608.0f), &sn, &cs);  // 2 frac
+        tab[s] = make_float4(q, cs, sn, 0.0f);
+    }
+    __syncthreads();
+    return tab;
+}
 
 // Tiled loop: entries [c0, c0 + m) of the global table into the warp's slot, copied
 // by the lanes in `mask` (the lanes that run the loop), 16 bytes per lane per step.
@@ -437,9 +457,10 @@ __device__ __forceinline__ LightFrame light_frame(f3 p, float4 Lp) {
 // Spherical light of radius R: sunflower point s of n on the great circle facing p,
 // radius R sqrt(s/n) at angle s * phi, phi = pi (3 - sqrt 5) (the angle is reduced
 // exactly as 2 pi frac(s (3 - sqrt 5) / 2) in 32-bit fixed point).
-// lf: light_frame(p, Lp) for a spherical light (unused otherwise).
+// lf: light_frame(p, Lp) for a spherical light (unused otherwise); flower: the
+// sunflower table of this frame's sample count, or null.
 __device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k, int l, int s, float4 Lp, float4 Ls,
-                                           uint4& w, const LightFrame& lf) {
+                                           uint4& w, const LightFrame& lf, const float4* flower) {
     if (Ls.x > 0.0f) {
         if ((s & 1) == 0)
             w = philox10(make_uint4(pix, (uint32_t)k, (uint32_t)l, (uint32_t)(s >> 1)), fr.key0, fr.key1);
@@ -450,10 +471,18 @@ __device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k,
         const float a = Ls.x, ginv = fr.sample_g_inv;
         return mk3(Lp.x + (((float)i + xi1) * ginv - 0.5f) * a, Lp.y, Lp.z + (((float)j + xi2) * ginv - 0.5f) * a);
     }
-    const float r = Ls.y * sqrtf((float)s / (float)fr.nsamp);
-    const uint32_t frac = (uint32_t)s * 0x61C88647u;  // 2^32 (3 - sqrt 5) / 2
-    float sn, cs;
-    sincospif((float)(frac >> 8) * (1.0f / 8388608.0f), &sn, &cs);  // 2 frac
+    float q, sn, cs;
+    if (flower) {
+        const float4 f = flower[s];
+        q = f.x;
+        cs = f.y;
+        sn = f.z;
+    } else {
+        q = sqrtf((float)s / (float)fr.nsamp);
+        const uint32_t frac = (uint32_t)s * 0x61C88647u;  // 2^32 (3 - sqrt 5) / 2
+        sincospif((float)(frac >> 8) * (1.0f / 8388608.0f), &sn, &cs);  // 2 frac
+    }
+    const float r = Ls.y * q;
     return add(xyz(Lp), add(scl(lf.u, r * cs), scl(lf.v, r * sn)));
 }
 
@@ -529,8 +558,9 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
                     lf = light_frame(p, Lp);
                     lf_l = l;
                 }
-                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf)
-                                                                   : xyz(Lp);
+                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f
+                                 ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf, sc.flower)
+                                 : xyz(Lp);
                 // V = X - p (p as hi + lo), W = V / |V|^2
                 const f3 V = sub(sub(X, p), p_lo);
                 sw[j] = scl(V, __frcp_rn(dot(V, V)));
@@ -634,8 +664,9 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                     lf = light_frame(p, Lp);
                     lf_l = l;
                 }
-                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf)
-                                                                   : xyz(Lp);
+                const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f
+                                 ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf, sc.flower)
+                                 : xyz(Lp);
                 // V = X - p (p as hi + lo), W = V / |V|^2
                 const f3 V = sub(sub(X, p), p_lo);
                 W = scl(V, __frcp_rn(dot(V, V)));
@@ -1147,8 +1178,9 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
             if (Ls.x > 0.0f && (s & 1))
                 w = philox10(make_uint4(pix, (uint32_t)k, (uint32_t)l, (uint32_t)(s >> 1)), fr.key0, fr.key1);
             const LightFrame lf = Ls.y > 0.0f ? light_frame(p, Lp) : LightFrame{};
-            const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf)
-                                                               : xyz(Lp);
+            const f3 X = nr > 1 || Ls.x > 0.0f || Ls.y > 0.0f
+                             ? sample_point(fr, pix, k, l, s, Lp, Ls, w, lf, sc.flower)
+                             : xyz(Lp);
             const f3 V = sub(sub(X, p), p_lo);
             W = scl(V, __frcp_rn(dot(V, V)));
             nv = scl(V, -1.0f);
