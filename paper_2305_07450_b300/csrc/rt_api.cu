@@ -1027,8 +1027,9 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         g_launches++;
         return cuda_status(cudaGetLastError());
     }
-    // the sunflower table of a spherical light's samples follows the staged data
-    const int flower_n = s->any_sphere_light ? p->shadow_samples : 0;
+    // the sunflower table of a spherical light's samples follows the staged data (from
+    // 16 samples on: with fewer, its set-up per CTA costs more than it saves)
+    const int flower_n = s->any_sphere_light && p->shadow_samples >= 16 ? p->shadow_samples : 0;
     const bool chunked = use_tiled_loop(L, s->ns_pad, (size_t)flower_n * 16);
     const uint32_t flower_off = (uint32_t)((stage_smem_bytes(chunked, s->ns_pad, nwarps) + 15) / 16 * 16);
     const size_t smem = flower_off + (size_t)flower_n * 16;
