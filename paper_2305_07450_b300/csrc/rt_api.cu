@@ -176,8 +176,9 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_p0_kernel(const SceneView sv, c
 // Pass k >= 1: persistent CTAs; each warp claims 32 entries of queue k at a time.
 // CTAs beyond the ones the queue's length needs return before staging.
 // A queue of at most wide_max paths (line-filter instances only) is taken one path
-// per warp (trace_queued_wide): such passes are bound by one warp's latency for one
-// hit, which spreading the hit's segments over the lanes cuts.
+// per warp (trace_queued_wide), each carried to its end: such passes are bound by
+// one warp's latency for one hit, which spreading the hit's segments over the lanes
+// cuts; the passes after a wide one find their queues empty.
 template <bool HITREC, int FM>
 __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv, const Frame fr, void* __restrict__ out,
                                                     size_t pitch, float* __restrict__ hr, size_t hr_plane,
@@ -211,7 +212,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv
                 if (lane == 0) i = atomicAdd(&ctl->head[k], 1u);
                 i = __shfl_sync(0xffffffffu, i, 0);
                 if (i >= n) break;
-                trace_queued_wide<HITREC>(sc, fr, cur.ent + (size_t)i * 4, k, nxt, out, pitch, hr, hr_plane);
+                trace_queued_wide<HITREC>(sc, fr, cur.ent + (size_t)i * 4, k, out, pitch, hr, hr_plane);
                 __syncwarp();
             }
             return;
