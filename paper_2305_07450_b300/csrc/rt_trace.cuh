@@ -491,8 +491,9 @@ __device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k,
 // spec_l; a light is skipped when n.l <= 0.  Phong spec = max(v.r, 0)^exp with r
 // the light direction mirrored about n and v = -d; Blinn spec = max(n.h, 0)^exp.
 // The shadow rays of the hit (one per lit point light, n per lit sampled light,
-// in light order) are traced in groups of up to four from the common origin po;
-// the group size is the warp's maximum of the lanes' remaining rays.
+// in light order) are traced in groups from the common origin po -- up to
+// kShadowGroup (4) with the segment test alone, kFiltGroup (7) through the line
+// filter; a group's size is the warp's maximum of the lanes' remaining rays.
 struct HitShade {
     float A, S;
 };
@@ -611,9 +612,10 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
 }
 
 // shade_hit for the staged brute-force kernels: the same shading, rays, Philox
-// counters and attribution, with the group's segments set up by a loop (one copy
-// of the sample code) that writes W and -V to shared memory and the unit vectors
-// for the filter to a local array, and every group tested by occluded_filtered.
+// counters and attribution, with groups of up to kFiltGroup segments set up by a
+// loop (one copy of the sample code) that writes W and -V to shared memory and the
+// unit vectors for the filter to a local array, and every group tested by
+// occluded_filtered.
 template <bool HITREC>
 __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, const Frame& fr, uint32_t pix, int k,
                                                      f3 p, f3 p_lo, f3 n, f3 po, f3 d, float ks, float e,
