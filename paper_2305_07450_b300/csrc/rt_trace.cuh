@@ -1,7 +1,10 @@
 // rt_trace.cuh -- per-pixel path of the Whitted ray tracer (arXiv 2305.07450,
 // Section 3) in FP32: primary ray, brute-force closest hit, shading with hard or
-// sampled shadows, register-resident reflection loop.  Shared by the per-frame
-// kernel, the batched persistent kernel and the adjoint's recompute mode.
+// sampled shadows (the segment test, and in front of it for large scenes a line
+// filter that decides most sphere-segment pairs in fewer operations with the same
+// verdict), register-resident reflection loop, and the bounce queues of the queued
+// render with their one-path-per-warp ("wide") form.  Shared by the per-frame and
+// queued kernels, the batched persistent kernel and the adjoint's recompute mode.
 #pragma once
 
 #include "rt_bvh.cuh"
