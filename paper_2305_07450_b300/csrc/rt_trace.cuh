@@ -241,11 +241,12 @@ __device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, u
 // would have said "not blocked", so every verdict is the segment test's, bit for
 // bit.  Why g <= 0 implies that (u = 2^-24; oc, V, r^2 the FP32 values both tests
 // use): the segment test's e is negative only if D^2 < r^2 (1 + 9u) (q = oc - u V
-// carries one rounding per component, e three).  V^ = V rsqrt(S), S = fl(V.V), is
-// within 4u of the unit vector componentwise, so the FP32 t' is within 7u |oc| of
-// oc.V^ and t'^2 >= |oc|^2 - D^2 - 14u |oc|^2; the filter's roundings cost at most
-// 5u |oc|^2 + 3u r^2.  With K1 = 1 - 64u and K2 = 1 + 64u, e < 0 gives
-// g > 45u |oc|^2 + 54u r^2 > 0.  The bound needs finite arithmetic: a pair whose
+// carries one rounding per component, e three).  V^ = V rsqrtf(S), S = fl(V.V), is
+// within 7u of the unit vector componentwise (S's rounding halved by the root, at
+// most 2 ulp for rsqrtf -- CUDA's documented bound -- and the product), so the FP32
+// t' is within 10u |oc| of oc.V^ and t'^2 >= |oc|^2 - D^2 - 20u |oc|^2; the filter's
+// roundings cost at most 5u |oc|^2 + 3u r^2.  With K1 = 1 - 64u and K2 = 1 + 64u,
+// e < 0 gives g > 39u |oc|^2 + 54u r^2 > 0.  The bound needs finite arithmetic: a pair whose
 // |oc|^2 exceeds 2^100 is flagged too, and a group whose S leaves [2^-60, 2^100]
 // for some lane takes the segment test throughout.  The flags are kept as the AND
 // of sign bits ("certainly clear" = every value negative), so NaN and +inf count
@@ -683,7 +684,7 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 if (!occj) {
                     const float S = dot(nv, nv);
                     ok = ok && S >= 0x1p-60f && S <= 0x1p100f;
-                    vn = scl(nv, -__frsqrt_rn(S));
+                    vn = scl(nv, -rsqrtf(S));  // V^ (the filter's bound allows 2 ulp)
                 }
                 if (++s == nr) {
                     s = 0;
@@ -1194,7 +1195,7 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
             if (!occj) {
                 const float S = dot(nv, nv);
                 ok = S >= 0x1p-60f && S <= 0x1p100f;
-                vn = scl(nv, -__frsqrt_rn(S));
+                vn = scl(nv, -rsqrtf(S));
             }
         }
         float vh[3 * kFiltGroup];
