@@ -372,7 +372,10 @@ size_t rt_backward_workspace_bytes(const rt_scene *scene, const rt_render_params
  *                no hit-record memory).
  *   workspace_dev: rt_backward_workspace_bytes bytes, 16-byte aligned.
  * Two launches (adjoint, then a fixed-order sum of the per-CTA partials): the
- * result is reproducible bit for bit. */
+ * result is reproducible bit for bit.  On return the workspace holds the partials,
+ * partial b (CTA b = blockIdx.y * grid_x + blockIdx.x) at floats [b G, b G + G);
+ * grad[e] = sum over w = 0..31 (in order) of s_w[e], s_w[e] = sum over b = w,
+ * w + 32, w + 64, ... (in order) of partial b's entry e, in FP32. */
 rt_status rt_render_backward(const rt_scene *scene, const rt_camera *cam, const rt_render_params *params,
                              const float *dl_dimg_dev, size_t dl_pitch_bytes, const void *hitrec_dev,
                              float *grad_dev, void *workspace_dev, size_t workspace_bytes,

@@ -1288,7 +1288,8 @@ rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_r
     g_launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
-    rt_grad_reduce_kernel<<<(G + 255) / 256, 256, 0, st_>>>(parts, (int)(grid.x * grid.y), G, grad_dev);
+    rt_grad_reduce_kernel<<<(G + 31) / 32, 32 * kReduceWarps, 0, st_>>>(parts, (int)(grid.x * grid.y), G,
+                                                                   grad_dev);
     g_launches++;
     return cuda_status(cudaGetLastError());
 }

@@ -20,8 +20,9 @@
 // Reduction (deterministic): within a warp, lanes that hit the same primitive are
 // summed by a fixed butterfly and the group's first lane adds the sum to the
 // warp's own table in shared memory; the CTA then sums its warps' tables in warp
-// order into one partial per CTA, and a second kernel sums the partials in CTA
-// order.  No floating-point atomics, so the result is reproducible bit for bit.
+// order into one partial per CTA, and a second kernel sums the partials in a fixed
+// order (rt_grad_reduce_kernel).  No floating-point atomics, so the result is
+// reproducible bit for bit.
 #pragma once
 
 #include "rt_errword.cuh"
@@ -308,14 +309,37 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
     }
 }
 
-// grad[e] = sum over CTAs b (in order) of partials[b][e].
-__global__ void rt_grad_reduce_kernel(const float* __restrict__ partials, int n_parts, int G,
-                                      float* __restrict__ grad) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= G) return;
-    float s = 0.0f;
-    for (int b = 0; b < n_parts; ++b) s += partials[(size_t)b * G + e];
-    grad[e] = s;
+// grad[e] = sum over CTAs b of partials[b][e], in a fixed order: a block owns 32
+// entries (one per lane) and its warp w sums the partials b = w, w + 32, w + 64, ...
+// in increasing b (8 loads in flight per lane); the 32 warp sums are then added in
+// warp order.  One thread per entry summing every partial in turn was bound by
+// load latency (thousands of dependent steps).
+constexpr int kReduceWarps = 32;
+__global__ void __launch_bounds__(32 * kReduceWarps) rt_grad_reduce_kernel(const float* __restrict__ partials,
+                                                                          int n_parts, int G,
+                                                                          float* __restrict__ grad) {
+    __shared__ float s[kReduceWarps][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    float acc = 0.0f;
+    if (e < G) {
+        int b = w;
+        for (; b + 7 * kReduceWarps < n_parts; b += 8 * kReduceWarps) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = __ldg(partials + (size_t)(b + j * kReduceWarps) * G + e);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc += v[j];
+        }
+        for (; b < n_parts; b += kReduceWarps) acc += __ldg(partials + (size_t)b * G + e);
+    }
+    s[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && e < G) {
+        float t = 0.0f;
+        for (int j = 0; j < kReduceWarps; ++j) t += s[j][lane];
+        grad[e] = t;
+    }
 }
 
 }  // namespace rtd

@@ -157,3 +157,31 @@ def test_backward_refuses_the_coupled_mode():
     dl = torch.zeros((32, 32, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(rt.RtError):
         rt.render_backward(ds, w.camera, w.params, dl)
+
+
+@pytest.mark.parametrize("W,H", [(264, 200), (96, 40)])
+def test_gradient_sum_over_cta_partials_in_its_stated_order(W, H):
+    """The second launch sums the per-CTA partials the workspace holds in the
+    order the header states (warp w: partials w, w + 32, ... in turn; then the 32
+    warp sums in turn), FP32: 425 partials (full groups of eight loads and a
+    ragged tail) and 18 (fewer partials than warps)."""
+    w = small_diff_workload(W, H)
+    ds = rt.DeviceScene(w.scene)
+    p = w.params
+    launch = {"block_x": 16, "block_y": 8}
+    dl = torch.randn((H, W, 4), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    G = rt.grad_count(ds)
+    n_parts = ((W + 15) // 16) * ((H + 7) // 8)
+    ws = torch.full((n_parts * G + 64,), float("nan"), dtype=torch.float32, device="cuda")
+    g = rt.render_backward(ds, w.camera, p, dl, hitrec=None, workspace=ws, launch=launch)
+    torch.cuda.synchronize()
+    ds.close()
+    parts = ws[: n_parts * G].view(n_parts, G).cpu().numpy()
+    assert np.isfinite(parts).all()
+    want = np.zeros(G, np.float32)
+    for wi in range(32):
+        acc = np.zeros(G, np.float32)
+        for b in range(wi, n_parts, 32):
+            acc = acc + parts[b]
+        want = want + acc
+    assert np.array_equal(g.cpu().numpy(), want)
