@@ -77,7 +77,9 @@ def inverse_render(init: scenes.Workload, target: torch.Tensor, steps: int = 200
     rp = init.params
     ds = rt.DeviceScene(init.scene)
     P = SceneParams(init.scene, optimize_centres)
-    opt = torch.optim.Adam([p for p in P.parameters() if p.requires_grad], lr=lr)
+    trainable = [p for p in P.parameters() if p.requires_grad]
+    # one fused kernel for every parameter instead of a sequence of foreach ops
+    opt = torch.optim.Adam(trainable, lr=lr, fused=all(p.is_cuda for p in trainable))
     start, history = 0, []
     if checkpoint and os.path.exists(checkpoint):
         st = torch.load(checkpoint, map_location="cuda")

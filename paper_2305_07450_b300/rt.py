@@ -488,25 +488,40 @@ def render_backward(dscene: DeviceScene, camera, params: scenes.Params, dl_dimg:
     return grad
 
 
+_UNPACK_INDEX: dict = {}
+
+
+def _unpack_index(n_spheres: int, n_lights: int, device) -> torch.Tensor:
+    """Gather map from the packed gradient (plus one appended zero, index G) to
+    the concatenated records [spheres N x 10 | plane 10 | lights L x 8]."""
+    key = (n_spheres, n_lights, str(device))
+    idx = _UNPACK_INDEX.get(key)
+    if idx is None:
+        N, L = n_spheres, n_lights
+        z = 8 * (N + 1) + 4 * L
+        sph = np.full((N, 10), z, np.int64)
+        base = 8 * np.arange(N, dtype=np.int64)[:, None]
+        sph[:, 0:3] = base + np.array([5, 6, 7])
+        sph[:, 4:8] = base + np.array([0, 1, 2, 3])
+        sph[:, 9] = base[:, 0] + 4
+        pl = np.full(10, z, np.int64)
+        pl[4:8] = 8 * N + np.arange(4)
+        pl[9] = 8 * N + 4
+        lig = np.full((L, 8), z, np.int64)
+        lig[:, 0:4] = 8 * (N + 1) + 4 * np.arange(L, dtype=np.int64)[:, None] + np.arange(4)
+        idx = torch.from_numpy(np.concatenate([sph.ravel(), pl, lig.ravel()])).to(device)
+        _UNPACK_INDEX[key] = idx
+    return idx
+
+
 def unpack_grad(grad: torch.Tensor, n_spheres: int, n_lights: int):
     """Packed gradient -> (spheres [N, 10], plane [10], lights [L, 8]) laid out
-    like the scene records (zeros where a field is not differentiated)."""
+    like the scene records (zeros where a field is not differentiated): one
+    gather through a cached index map."""
     N, L = n_spheres, n_lights
-    gs = grad[: 8 * N].view(N, 8)
-    gp = grad[8 * N: 8 * N + 8]
-    gl = grad[8 * (N + 1):].view(L, 4)
-    sph = torch.zeros((N, 10), dtype=grad.dtype, device=grad.device)
-    sph[:, 0:3] = gs[:, 5:8]
-    sph[:, 4:7] = gs[:, 0:3]
-    sph[:, 7] = gs[:, 3]
-    sph[:, 9] = gs[:, 4]
-    pl = torch.zeros(10, dtype=grad.dtype, device=grad.device)
-    pl[4:7] = gp[0:3]
-    pl[7] = gp[3]
-    pl[9] = gp[4]
-    lig = torch.zeros((L, 8), dtype=grad.dtype, device=grad.device)
-    lig[:, 0:4] = gl
-    return sph, pl, lig
+    G = 8 * (N + 1) + 4 * L
+    flat = torch.cat([grad[:G], grad.new_zeros(1)])[_unpack_index(N, L, grad.device)]
+    return flat[: 10 * N].view(N, 10), flat[10 * N: 10 * N + 10], flat[10 * N + 10:].view(L, 8)
 
 
 class RenderFn(torch.autograd.Function):
