@@ -28,6 +28,7 @@ struct StagedScene {
     BvhView bvh;           // hierarchy over the spheres (ACC kernels only)
     SkyView sky;           // panorama of the misses (null: black)
     const float4* flower;  // shared sunflower table (sunflower_table), or null: computed per sample
+    float cone_r2 = 0.0f;  // rho^2 of the cone pre-pass (staged_cone_r2), or 0: no pre-pass
 };
 
 // The sunflower points of a spherical light that do not depend on the hit: for
@@ -270,6 +271,100 @@ struct SegFilt {  // V^ of a segment in both halves
     float2 vx, vy, vz;
 };
 
+// Cone pre-pass of a sampled light (square area light or spherical light).  All the
+// light's segments start at the shadow origin o and run along V_j = X_j - p towards
+// sample points X_j of a small region, so their unit vectors lie within an angle
+// alpha = arccos(kappa) of one axis a: every segment's line lies in the double cone
+// {o + x : |x.a| >= |x| cos alpha}.  A sphere whose centre is farther than rho from
+// that cone is farther than rho from every one of the lines, and the segment test
+// reports a block only at a line distance D with D^2 < r^2 (1 + 9u) (the line
+// filter's bound), so rho^2 >= r_max^2 (1 + 9u) over the table suffices.  With t =
+// oc.a (a of unit length) and d^2 = |oc|^2 - t^2, the distance to the double cone is
+// d kappa - |t| sin alpha where positive; "d kappa - |t| sin alpha < rho", squared
+// (both sides non-negative) and with sin alpha replaced by sigma >= sin alpha, gives
+// the necessary condition kappa^2 |oc|^2 - t^2 < rho^2 + 2 rho sigma |t|.  The pass
+// evaluates h = t^2 + 2 rho sigma |t| + rho^2 - (kappa^2 - 2^-16) |oc|^2 per sphere
+// pair (t: 3 packed FMAs, h: 3) and calls a pair clear when h < 0 in both halves and
+// |oc|^2 < 2^100.  Error budget (u = 2^-24): the FP32 axis is within 6u of unit length
+// and direction, so the computed t is within 10u |oc| of the exact projection; t^2,
+// the |t| term, |oc|^2 and the three roundings of h add at most 50u |oc|^2 + 20u rho^2,
+// below the 2^-16 |oc|^2 taken off kappa^2 and the 2^-14 rho^2 added to r_max^2.
+// NaN (canonical, positive) and +inf never clear.  A warp keeps one bit per block of
+// kPad spheres, set when some lane's cone is not clear of some pair of the block.  A
+// group whose every segment belongs to the cone's light, each V^ checked to satisfy
+// V^.a >= kappa + 2^-12 (the check's roundings stay below 25u), visits only the
+// blocks whose bit is set: a skipped block could block none of its segments, so every
+// verdict is the segment test's, bit for bit.
+constexpr int kConeWords = 16;                        // bits per warp: 32 * kConeWords blocks
+// The cone light's segments go in groups of kConeGroup, and every group of at most
+// kConeGroup segments (the point lights' too, unused slots counting as blocked) runs
+// through the one instance occluded_filtered<kConeGroup>: with the pre-pass a group
+// visits few blocks, and a hit whose groups ran three instances (3, 7 and 2 segments
+// for the 4K scene's 3 + 16) stalled on instruction fetch (ncu: no_instruction 2.69
+// stalls per issue against 0.29).  Measured on B300, 4K queued frame, groups of 7 /
+// 4 with their own instances / 3, 4, 5, 6 through one instance: 8.03 / 7.60 / 6.97,
+// 6.91, 7.32, 7.51 ms.
+constexpr int kConeGroup = 4;
+constexpr int kConeMaxPad = 32 * kConeWords * kPad;   // larger tables take no pre-pass
+__shared__ uint32_t s_cone[(kSegStride / 32) * kConeWords];
+__shared__ unsigned s_r2max;
+
+// rho^2 of the pre-pass: the largest r^2 of the staged table times (1 + 2^-14) (pad
+// entries, -r^2 = +1, fall out), or 0 (no pre-pass) for tables of more than
+// kConeMaxPad entries or when it leaves (0, 2^60].  Every thread of the CTA calls.
+__device__ __forceinline__ float staged_cone_r2(const float4* geo, int ns_pad) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nth = blockDim.x * blockDim.y;
+    if (tid == 0) s_r2max = 0u;
+    __syncthreads();
+    float m = 0.0f;
+    for (int q = tid; q < ns_pad / 2; q += nth) {
+        const float4 B = geo[2 * q + 1];
+        m = fmaxf(m, fmaxf(-B.z, -B.w));
+    }
+    if (m > 0.0f) atomicMax(&s_r2max, __float_as_uint(m));  // non-negative floats order as their bits
+    __syncthreads();
+    const float r2 = __uint_as_float(s_r2max) * (1.0f + 0x1p-14f);
+    return (ns_pad <= kConeMaxPad && r2 > 0.0f && r2 <= 0x1p60f) ? r2 : 0.0f;
+}
+
+// The warp's block bits for the cones of the lanes in `mask` whose `use` is set
+// (axis ax, c0 = kappa^2 - 2^-16, twors = 2 rho sigma), written to cw[0 .. n / kPad
+// / 32].  Out of line: the shading code keeps its registers.
+__device__ __noinline__ void cone_pass(const float4* __restrict__ geo, int n, unsigned mask, f3 o, f3 ax, float c0,
+                                       float twors, float rho2, bool use, uint32_t* cw) {
+    const RayPair o2 = ray_pair(o);
+    const float2 axx = dup2(ax.x), axy = dup2(ax.y), axz = dup2(ax.z);
+    const float2 nc0 = dup2(-c0), tw = dup2(twors), r2 = dup2(rho2);
+    const int nb = n / kPad;
+    const bool leader = (threadIdx.x & 31) == __ffs(mask) - 1;
+#pragma unroll 1
+    for (int w0 = 0; w0 < nb; w0 += 32) {
+        uint32_t word = 0;
+        const int m = min(32, nb - w0);
+#pragma unroll 1
+        for (int b = 0; b < m; ++b) {
+            const float4* g = geo + (size_t)(w0 + b) * kPad;
+            uint32_t clr = 0xffffffffu;
+#pragma unroll
+            for (int q = 0; q < kPad / 2; ++q) {
+                const float4 A = g[2 * q], B = g[2 * q + 1];
+                const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
+                const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
+                const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
+                const float2 oc2 = fma2(ocx, ocx, fma2(ocy, ocy, mul2(ocz, ocz)));
+                const float2 big = add2(oc2, dup2(-0x1p100f));
+                const float2 t = fma2(ocx, axx, fma2(ocy, axy, mul2(ocz, axz)));
+                const float2 at = make_float2(fabsf(t.x), fabsf(t.y));
+                const float2 h = fma2(oc2, nc0, fma2(t, t, fma2(at, tw, r2)));
+                clr &= __float_as_uint(h.x) & __float_as_uint(h.y) & __float_as_uint(big.x) & __float_as_uint(big.y);
+            }
+            word |= (__any_sync(mask, use && (clr >> 31) == 0) ? 1u : 0u) << b;
+        }
+        if (leader) cw[w0 >> 5] = word;
+    }
+    __syncwarp(mask);
+}
+
 // Segment test of pair q (spheres 2q, 2q + 1 of geo) against the R segments, the
 // operations of occluded_block; W and -V from shared memory (seg[k * kSegStride],
 // k = 6 r + (0..2: W, 3..5: -V)).
@@ -344,10 +439,12 @@ __device__ __forceinline__ bool occluded_block_filtered(const float4* __restrict
 // already blocked); blocked_in / the result: bit r = segment r blocked.  The
 // caller has written W and -V to seg (shared memory).  exact_only: the segment
 // test for every pair (a group for which the filter's bound is not established).
+// cone: the warp's block bits of the cone pre-pass (only the blocks whose bit is set
+// are visited), or null (every block).
 template <int R>
 __device__ __noinline__ uint32_t occluded_filtered(const float4* __restrict__ geo, int n, unsigned mask, f3 o,
                                                    const float* __restrict__ vh, uint32_t blocked_in,
-                                                   const float* seg, bool exact_only) {
+                                                   const float* seg, bool exact_only, const uint32_t* cone) {
     const RayPair o2 = ray_pair(o);
     SegFilt sf[kFiltGroup];
     uint32_t acc[kFiltGroup];
@@ -368,9 +465,21 @@ __device__ __noinline__ uint32_t occluded_filtered(const float4* __restrict__ ge
             if (__all_sync(mask, done)) break;
         }
     } else {
+        const int nb = n / kPad;
+        bool stop = false;
 #pragma unroll 1
-        for (int i0 = 0; i0 < n; i0 += kPad)
-            if (occluded_block_filtered<R>(geo + i0, mask, o2, sf, seg, acc)) break;
+        for (int w0 = 0; w0 < nb && !stop; w0 += 32) {
+            uint32_t m = cone ? cone[w0 >> 5] : (nb - w0 >= 32 ? 0xffffffffu : (1u << (nb - w0)) - 1u);
+#pragma unroll 1
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1u;
+                if (occluded_block_filtered<R>(geo + (size_t)(w0 + b) * kPad, mask, o2, sf, seg, acc)) {
+                    stop = true;
+                    break;
+                }
+            }
+        }
     }
     uint32_t out = 0;
 #pragma unroll
@@ -628,12 +737,18 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
     HitShade out{fr.ka, 0.0f};
     uint32_t lit = 0;
     int total = 0;
+    int lc = -1, before_lc = 0;  // the cone pre-pass's light (first lit sampled light), segments before it
 #pragma unroll 1
     for (int li = 0; li < h.nl; ++li) {
         const f3 lh = normalize_rn(sub(sub(xyz(h.light_p[li]), p), p_lo));
         if (dot(n, lh) > 0.0f) {
             lit |= 1u << li;
-            total += rays_of_light(fr, h.light_s[li]);
+            const int nr = rays_of_light(fr, h.light_s[li]);
+            if (lc < 0 && nr > 1) {
+                lc = li;
+                before_lc = total;
+            }
+            total += nr;
         }
         if (HITREC) hr[hr_k + (size_t)(2 + li) * hr_plane] = 0.0f;
     }
@@ -650,22 +765,61 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
     const bool plane = h.has_plane != 0;
     const f3 pn = xyz(h.plane_g);
     const float num = -(dot(po, pn) + h.plane_g.w);
+    // cone of light lc seen from p (cone_pass): axis towards its centre, kappa below
+    // the cosine to every point of its sample region (the square's corners; the
+    // tangent cone of a spherical light), less 2^-11
+    f3 ax = mk3(0.f, 0.f, 0.f);
+    float kap = 0.0f;
+    bool cone_ok = false;
+    if (lc >= 0 && sc.cone_r2 > 0.0f) {
+        const float4 Lp = h.light_p[lc], Ls = h.light_s[lc];
+        const f3 Lv = sub(sub(xyz(Lp), p), p_lo);
+        float dist;
+        ax = normalize_rn(Lv, &dist);
+        if (Ls.x > 0.0f) {
+            const float hs = 0.5f * Ls.x;
+            kap = 1.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const f3 cv = add(Lv, mk3((c & 1) ? hs : -hs, 0.0f, (c & 2) ? hs : -hs));
+                kap = fminf(kap, dot(ax, cv) * rsqrtf(dot(cv, cv)));
+            }
+        } else {
+            const float sr = Ls.y / dist;
+            kap = sqrtf(fmaxf(fmaf(-sr, sr, 1.0f), 0.0f));
+        }
+        kap -= 0x1p-11f;
+        cone_ok = kap >= 0.5f;  // NaN: false
+    }
+    const bool cone_any = __any_sync(mask, cone_ok);
+    uint32_t* cw = s_cone + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5) * kConeWords;
+    if (cone_any) {
+        const float sg = sqrtf(fmaxf(fmaf(-kap, kap, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);  // >= sin alpha
+        cone_pass(sc.geo, h.ns_pad, mask, po, ax, fmaf(kap, kap, -0x1p-16f), 2.0f * sqrtf(sc.cone_r2) * sg,
+                  sc.cone_r2, cone_ok, cw);
+    }
+    const float kv = kap + 0x1p-12f;
 #pragma unroll 1
     while (true) {
-        const int kr = min(kFiltGroup, total - done);
+        // a group ends before the cone light's first segment, so that its segments
+        // form groups of their own (of kConeGroup)
+        const int lim = cone_ok && done < before_lc ? before_lc : total;
+        const int kr = min(cone_ok && done >= before_lc ? kConeGroup : kFiltGroup, lim - done);
         const int R = (int)__reduce_max_sync(mask, (unsigned)kr);
         if (R == 0) break;
         float vh[3 * kFiltGroup];
         uint32_t blocked = 0;
         bool ok = true;
+        bool pure = cone_ok || kr == 0;  // every segment of the group inside the cone of light lc
 #pragma unroll 1
-        for (int j = 0; j < R; ++j) {  // occluded_filtered<R> reads slots 0..R-1
+        for (int j = 0; j < (R <= kConeGroup ? kConeGroup : R); ++j) {  // slots read by the instance below
             f3 W = mk3(0.f, 0.f, 0.f), nv = mk3(0.f, 0.f, 0.f), vn = mk3(0.f, 0.f, 0.f);
             bool occj = true;
             if (j < kr) {
                 const float4 Lp = h.light_p[l];
                 const float4 Ls = h.light_s[l];
                 const int nr = rays_of_light(fr, Ls);
+                pure = pure && l == lc;
                 if (Ls.y > 0.0f && lf_l != l) {
                     lf = light_frame(p, Lp);
                     lf_l = l;
@@ -685,6 +839,7 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                     const float S = dot(nv, nv);
                     ok = ok && S >= 0x1p-60f && S <= 0x1p100f;
                     vn = scl(nv, -rsqrtf(S));  // V^ (the filter's bound allows 2 ulp)
+                    pure = pure && dot(ax, vn) >= kv;
                 }
                 if (++s == nr) {
                     s = 0;
@@ -705,16 +860,15 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
             g[5 * kSegStride] = nv.z;
         }
         const bool exact_only = !__all_sync(mask, ok);
-        static_assert(kFiltGroup >= 4 && kFiltGroup <= 8, "dispatch below");
+        const uint32_t* cone = cone_any && __all_sync(mask, pure) ? cw : nullptr;
+        static_assert(kFiltGroup >= 4 && kFiltGroup <= 8 && kConeGroup == 4, "dispatch below");
         constexpr int G = kFiltGroup;
-        if (R == 1) blocked = occluded_filtered<1>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
-        else if (R == 2) blocked = occluded_filtered<2>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
-        else if (R == 3) blocked = occluded_filtered<3>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
-        else if (R == 4) blocked = occluded_filtered<4>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
-        else if (R == 5) blocked = occluded_filtered<(G < 5 ? G : 5)>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
-        else if (R == 6) blocked = occluded_filtered<(G < 6 ? G : 6)>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
-        else if (R == 7) blocked = occluded_filtered<(G < 7 ? G : 7)>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
-        else blocked = occluded_filtered<G>(sc.geo, h.ns_pad, mask, po, vh, blocked, seg, exact_only);
+        const int np = h.ns_pad;
+        if (R <= kConeGroup) blocked = occluded_filtered<kConeGroup>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
+        else if (R == 5) blocked = occluded_filtered<(G < 5 ? G : 5)>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
+        else if (R == 6) blocked = occluded_filtered<(G < 6 ? G : 6)>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
+        else if (R == 7) blocked = occluded_filtered<(G < 7 ? G : 7)>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
+        else blocked = occluded_filtered<G>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
         // attribute the results to their lights in the same order
 #pragma unroll 1
         for (int j = 0; j < kr; ++j) {
@@ -1210,7 +1364,7 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
         seg[5 * kSegStride] = nv.z;
         const bool exact_only = !__all_sync(0xffffffffu, ok);
         const uint32_t blocked = occluded_filtered<1>(sc.geo, h.ns_pad, 0xffffffffu, po, vh, occj ? 1u : 0u, seg,
-                                                      exact_only);
+                                                      exact_only, nullptr);
         const bool vis = valid && !(blocked & 1u);
 #pragma unroll
         for (int li = 0; li < RT_MAX_LIGHTS; ++li)

@@ -110,3 +110,80 @@ def test_sampled_spherical_light_and_4k_scene_crop():
     w = S.area_4k()
     w.params.width, w.params.height = 480, 270
     assert_filter_exact(w.scene, w.camera, w.params)
+
+
+# ---- the cone pre-pass of sampled lights (cone_pass): skipped sphere blocks change
+# no verdict.  Every case below is compared with the tiled loop, which has neither
+# the filter nor the pre-pass.
+
+def test_cone_boundary_shell_of_a_square_light():
+    """Spheres tangent to the segments from plane points to the corners of a square
+    light (the cone's boundary), pushed 1e-3, 1e-6 or 0 outwards or inwards, plus
+    filler: blocks just inside and just outside every lane's cone."""
+    L, side = np.array([0.5, 9.0, -0.5]), 3.0
+    corners = [L + np.array([sx * side / 2, 0.0, sz * side / 2]) for sx in (-1, 1) for sz in (-1, 1)]
+    rng = np.random.default_rng(11)
+    sph = []
+    deltas = (-1e-3, -1e-6, 0.0, 1e-6, 1e-3)
+    for i, px in enumerate(np.linspace(-3, 3, 6)):
+        for j, pz in enumerate(np.linspace(-3, 3, 6)):
+            p0 = np.array([px, 0.0, pz])
+            axis = L - p0
+            axis /= np.linalg.norm(axis)
+            k = (i * 6 + j) % 4
+            v = corners[k] - p0
+            a = 0.25 + 0.15 * ((i + 2 * j) % 4)
+            q = p0 + a * v
+            out = np.cross(np.cross(axis, v), v)        # perpendicular to v, away from the axis
+            out *= -np.sign(np.dot(out, axis)) / np.linalg.norm(out)
+            r = float(rng.uniform(0.1, 0.4))
+            c = q + out * (r + deltas[(i + j) % 5])
+            sph.append(sphere(tuple(c), r, albedo=tuple(rng.random(3)), refl=0.3))
+    while len(sph) < 160:
+        sph.append(sphere((rng.uniform(-6, 6), rng.uniform(0.4, 4), rng.uniform(-6, 6)), rng.uniform(0.15, 0.7),
+                          albedo=tuple(rng.random(3)), refl=rng.uniform(0, 0.5)))
+    sc, cam, p = mk(spheres=sph, plane=plane_rec(refl=0.2),
+                    lights=[light((-4, 8, 3), 0.6), light(tuple(L), 0.9, side)],
+                    camera=(0, 7, -10, 0, -32, 60), W=256, H=176, D=3, samples=16, seed=21)
+    assert_filter_exact(sc, cam, p)
+
+
+def test_cone_spherical_light_near_the_scene():
+    """A spherical light whose radius is close to its distance from part of the
+    scene: lanes of one warp with and without a usable cone."""
+    sc, cam, p = cluster_scene(seed=12)
+    L, R = np.array([0.3, 2.4, -0.2]), 1.4
+    sph = sc.spheres.astype(np.float64)
+    keep = np.linalg.norm(sph[:, :3] - L, axis=1) - R > sph[:, 3] + 0.05   # the light outside every sphere
+    sph = sph[keep]
+    rng = np.random.default_rng(12)
+    while len(sph) < 128:
+        sph = np.vstack([sph, sphere((rng.uniform(-6, 6), rng.uniform(0.5, 2), rng.uniform(6, 10)), 0.4)])
+    sc.spheres = S.f32(sph)
+    sc.lights[1, :3] = S.f32(L)
+    sc.lights[1, 4], sc.lights[1, 5] = 0.0, R
+    p.shadow_samples = 25
+    assert_filter_exact(sc, cam, p)
+
+
+@pytest.mark.parametrize("n", [4096, 4100])
+def test_cone_table_size_limit(n):
+    """4096 spheres (the largest table with a pre-pass) and 4100 (padded to 4104:
+    none), with a square light."""
+    rng = np.random.default_rng(n)
+    sph = [sphere((rng.uniform(-30, 30), rng.uniform(0.3, 3), rng.uniform(-30, 30)), rng.uniform(0.2, 0.6),
+                  albedo=tuple(rng.random(3)), refl=rng.uniform(0, 0.4)) for _ in range(n)]
+    sc, cam, p = mk(spheres=sph, plane=plane_rec(refl=0.2), lights=[light((2, 20, -4), 0.8, 4.0)],
+                    camera=(0, 12, -40, 0, -18, 60), W=128, H=72, D=2, samples=16, seed=5)
+    assert_filter_exact(sc, cam, p)
+
+
+def test_cone_with_huge_coordinates():
+    """Spheres 1e20 away (|oc|^2 overflows) with finite radii: the pre-pass stays on
+    and must not clear their blocks by overflow."""
+    sc, cam, p = cluster_scene(seed=13)
+    sph = sc.spheres.copy()
+    sph[:5, 0] = S.f32([1e20, -1e20, 3e19, 1e20, -5e19])
+    sph[:5, 2] = S.f32([1e20, 1e20, -1e20, -2e20, 5e19])
+    sc.spheres = sph
+    assert_filter_exact(sc, cam, p)
