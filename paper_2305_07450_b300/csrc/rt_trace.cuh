@@ -292,9 +292,14 @@ struct SegFilt {  // V^ of a segment in both halves
 // NaN (canonical, positive) and +inf never clear.  A warp keeps one bit per block of
 // kPad spheres, set when some lane's cone is not clear of some pair of the block.  A
 // group whose every segment belongs to the cone's light, each V^ checked to satisfy
-// V^.a >= kappa + 2^-12 (the check's roundings stay below 25u), visits only the
-// blocks whose bit is set: a skipped block could block none of its segments, so every
-// verdict is the segment test's, bit for bit.
+// V^.a >= kappa + 2^-18 (the check's roundings stay below 25u = 2^-18 / 2.5), visits
+// only the blocks whose bit is set: a skipped block could block none of its segments,
+// so every verdict is the segment test's, bit for bit.  The warp's coarse pass uses
+// one cone for all lanes (apex p0 = one lane's shadow origin): a lane's blocking
+// sphere lies within rho of its segment (the segment test's u is in [0, 1]), the
+// segment lies in the lane's cone at its apex po, that cone in the warp's cone moved
+// to po, hence the sphere within rho + |po - p0| of the warp's cone, up to the
+// roundings of c - po and c - p0 (2u |oc|, inside the same |oc|^2 slack).
 constexpr int kConeWords = 16;                        // bits per warp: 32 * kConeWords blocks
 // The cone light's segments go in groups of kConeGroup, and every group of at most
 // kConeGroup segments (the point lights' too, unused slots counting as blocked) runs
@@ -327,39 +332,69 @@ __device__ __forceinline__ float staged_cone_r2(const float4* geo, int ns_pad) {
     return (ns_pad <= kConeMaxPad && r2 > 0.0f && r2 <= 0x1p60f) ? r2 : 0.0f;
 }
 
-// The warp's block bits for the cones of the lanes in `mask` whose `use` is set
-// (axis ax, c0 = kappa^2 - 2^-16, twors = 2 rho sigma), written to cw[0 .. n / kPad
-// / 32].  Out of line: the shading code keeps its registers.
+// True when the cone (apex o via o2, axis ax, c0 = kappa^2 - 2^-16, tw = 2 rho sigma,
+// r2 = rho^2) is clear of every pair of the block of kPad spheres at g.
+__device__ __forceinline__ bool cone_block_clear(const float4* __restrict__ g, const RayPair& o2, float2 axx,
+                                                 float2 axy, float2 axz, float2 nc0, float2 tw, float2 r2) {
+    uint32_t clr = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < kPad / 2; ++q) {
+        const float4 A = g[2 * q], B = g[2 * q + 1];
+        const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
+        const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
+        const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
+        const float2 oc2 = fma2(ocx, ocx, fma2(ocy, ocy, mul2(ocz, ocz)));
+        const float2 big = add2(oc2, dup2(-0x1p100f));
+        const float2 t = fma2(ocx, axx, fma2(ocy, axy, mul2(ocz, axz)));
+        const float2 at = make_float2(fabsf(t.x), fabsf(t.y));
+        const float2 h = fma2(oc2, nc0, fma2(t, t, fma2(at, tw, r2)));
+        clr &= __float_as_uint(h.x) & __float_as_uint(h.y) & __float_as_uint(big.x) & __float_as_uint(big.y);
+    }
+    return (clr >> 31) != 0;
+}
+
+// The warp's block bits for the cones of the lanes in `mask` whose `use` is set (this
+// lane's cone: apex o, axis ax, c0, twors, rho2), written to cw[0 .. n / kPad / 32].
+// With `coarse`, a first pass splits the blocks over the lanes and tests each once
+// against the warp's cone (apex p0, axis aw, wc0, wtw, wr2), which holds every
+// lane's cone moved to p0 (its width covers each lane's axis offset plus its width,
+// its radius rho plus the farthest lane apex): only the blocks it does not clear
+// are tested against the lanes' own cones.  Out of line: the shading code keeps its
+// registers.
 __device__ __noinline__ void cone_pass(const float4* __restrict__ geo, int n, unsigned mask, f3 o, f3 ax, float c0,
-                                       float twors, float rho2, bool use, uint32_t* cw) {
+                                       float twors, float rho2, bool use, uint32_t* cw, f3 p0, f3 aw, float wc0,
+                                       float wtw, float wr2, bool coarse) {
+    const int lane = threadIdx.x & 31;
+    const int nb = n / kPad;
+    const bool leader = lane == __ffs(mask) - 1;
+    if (coarse) {
+        const int rank = __popc(mask & ((1u << lane) - 1u)), cnt = __popc(mask);
+        for (int w = rank; w < (nb + 31) / 32; w += cnt) cw[w] = 0u;
+        __syncwarp(mask);
+        const RayPair q2 = ray_pair(p0);
+        const float2 bx = dup2(aw.x), by = dup2(aw.y), bz = dup2(aw.z);
+        const float2 bc0 = dup2(-wc0), btw = dup2(wtw), br2 = dup2(wr2);
+#pragma unroll 1
+        for (int b = rank; b < nb; b += cnt)
+            if (!cone_block_clear(geo + (size_t)b * kPad, q2, bx, by, bz, bc0, btw, br2))
+                atomicOr(&cw[b >> 5], 1u << (b & 31));
+        __syncwarp(mask);
+    }
     const RayPair o2 = ray_pair(o);
     const float2 axx = dup2(ax.x), axy = dup2(ax.y), axz = dup2(ax.z);
     const float2 nc0 = dup2(-c0), tw = dup2(twors), r2 = dup2(rho2);
-    const int nb = n / kPad;
-    const bool leader = (threadIdx.x & 31) == __ffs(mask) - 1;
 #pragma unroll 1
     for (int w0 = 0; w0 < nb; w0 += 32) {
+        uint32_t m = coarse ? cw[w0 >> 5] : (nb - w0 >= 32 ? 0xffffffffu : (1u << (nb - w0)) - 1u);
         uint32_t word = 0;
-        const int m = min(32, nb - w0);
 #pragma unroll 1
-        for (int b = 0; b < m; ++b) {
-            const float4* g = geo + (size_t)(w0 + b) * kPad;
-            uint32_t clr = 0xffffffffu;
-#pragma unroll
-            for (int q = 0; q < kPad / 2; ++q) {
-                const float4 A = g[2 * q], B = g[2 * q + 1];
-                const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
-                const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
-                const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
-                const float2 oc2 = fma2(ocx, ocx, fma2(ocy, ocy, mul2(ocz, ocz)));
-                const float2 big = add2(oc2, dup2(-0x1p100f));
-                const float2 t = fma2(ocx, axx, fma2(ocy, axy, mul2(ocz, axz)));
-                const float2 at = make_float2(fabsf(t.x), fabsf(t.y));
-                const float2 h = fma2(oc2, nc0, fma2(t, t, fma2(at, tw, r2)));
-                clr &= __float_as_uint(h.x) & __float_as_uint(h.y) & __float_as_uint(big.x) & __float_as_uint(big.y);
-            }
-            word |= (__any_sync(mask, use && (clr >> 31) == 0) ? 1u : 0u) << b;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            const bool clear = cone_block_clear(geo + (size_t)(w0 + b) * kPad, o2, axx, axy, axz, nc0, tw, r2);
+            word |= (__any_sync(mask, use && !clear) ? 1u : 0u) << b;
         }
+        __syncwarp(mask);  // every lane has read the coarse word
         if (leader) cw[w0 >> 5] = word;
     }
     __syncwarp(mask);
@@ -767,7 +802,7 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
     const float num = -(dot(po, pn) + h.plane_g.w);
     // cone of light lc seen from p (cone_pass): axis towards its centre, kappa below
     // the cosine to every point of its sample region (the square's corners; the
-    // tangent cone of a spherical light), less 2^-11
+    // tangent cone of a spherical light), less 2^-17
     f3 ax = mk3(0.f, 0.f, 0.f);
     float kap = 0.0f;
     bool cone_ok = false;
@@ -788,17 +823,45 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
             const float sr = Ls.y / dist;
             kap = sqrtf(fmaxf(fmaf(-sr, sr, 1.0f), 0.0f));
         }
-        kap -= 0x1p-11f;
+        kap -= 0x1p-17f;
         cone_ok = kap >= 0.5f;  // NaN: false
     }
-    const bool cone_any = __any_sync(mask, cone_ok);
     uint32_t* cw = s_cone + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5) * kConeWords;
-    if (cone_any) {
-        const float sg = sqrtf(fmaxf(fmaf(-kap, kap, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);  // >= sin alpha
-        cone_pass(sc.geo, h.ns_pad, mask, po, ax, fmaf(kap, kap, -0x1p-16f), 2.0f * sqrtf(sc.cone_r2) * sg,
-                  sc.cone_r2, cone_ok, cw);
+    unsigned cm = __ballot_sync(mask, cone_ok);
+    if (cm) {
+        // the warp's cone: apex and axis of the first lane with a cone; lanes whose
+        // cone light differs from that lane's drop out of the pre-pass
+        const int ld = __ffs(cm) - 1;
+        const int lw = __shfl_sync(mask, lc, ld);
+        const f3 p0 = mk3(__shfl_sync(mask, po.x, ld), __shfl_sync(mask, po.y, ld), __shfl_sync(mask, po.z, ld));
+        const f3 aw = mk3(__shfl_sync(mask, ax.x, ld), __shfl_sync(mask, ax.y, ld), __shfl_sync(mask, ax.z, ld));
+        cone_ok = cone_ok && lc == lw;
+        cm = __ballot_sync(mask, cone_ok);
+        const float sa = sqrtf(fmaxf(fmaf(-kap, kap, 1.0f), 0.0f));
+        // cos(beta + alpha), beta the angle between this lane's axis and aw, less a
+        // margin; the distance from p0 to this lane's apex
+        float kw = 1.0f, dw = 0.0f;
+        if (cone_ok) {
+            const float cb = fminf(dot(ax, aw), 1.0f);
+            const float sb = sqrtf(fmaxf(fmaf(-cb, cb, 1.0f), 0.0f));
+            kw = fmaf(cb, kap, -sb * sa) - 0x1p-17f;
+            kw = kw >= 0.5f ? kw : 0.0f;  // NaN: 0
+            const f3 dp = sub(po, p0);
+            dw = sqrtf(dot(dp, dp));
+        }
+        // warp minimum / maximum (non-negative floats order as their bits)
+        const float kwm = __uint_as_float(__reduce_min_sync(mask, __float_as_uint(kw)));
+        const float dwm = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(dw)));
+        const bool coarse = kwm >= 0.5f && dwm <= 0x1p30f;
+        const float rho = sqrtf(sc.cone_r2);
+        const float rw = (rho + dwm) * (1.0f + 0x1p-15f);
+        const float sw = sqrtf(fmaxf(fmaf(-kwm, kwm, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
+        const float sg = sa * (1.0f + 0x1p-18f);  // >= sin alpha
+        cone_pass(sc.geo, h.ns_pad, mask, po, ax, fmaf(kap, kap, -0x1p-16f), 2.0f * rho * sg, sc.cone_r2, cone_ok, cw,
+                  p0, aw, fmaf(kwm, kwm, -0x1p-16f), 2.0f * rw * sw, rw * rw * (1.0f + 0x1p-15f), coarse);
     }
-    const float kv = kap + 0x1p-12f;
+    const bool cone_any = cm != 0;
+    const float kv = kap + 0x1p-18f;
 #pragma unroll 1
     while (true) {
         // a group ends before the cone light's first segment, so that its segments
