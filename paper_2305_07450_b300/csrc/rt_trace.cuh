@@ -28,7 +28,8 @@ struct StagedScene {
     BvhView bvh;           // hierarchy over the spheres (ACC kernels only)
     SkyView sky;           // panorama of the misses (null: black)
     const float4* flower;  // shared sunflower table (sunflower_table), or null: computed per sample
-    float cone_r2 = 0.0f;  // rho^2 of the cone pre-pass (staged_cone_r2), or 0: no pre-pass
+    float cone_r2 = 0.0f;  // rho^2 of the cone pre-pass (staged_cone), or 0: no pre-pass
+    float cone_cmax = 0.0f;  // bound on the centres' |c| (staged_cone)
 };
 
 // The sunflower points of a spherical light that do not depend on the hit: for
@@ -142,8 +143,11 @@ __device__ __forceinline__ void closest_block(const float4* __restrict__ geo, in
     }
 }
 
+// blocks: the blocks of kPad spheres to test (bits, ray_cull), or null: every
+// block (the staged table only; visited in index order either way).
 template <bool CH, bool ACC = false>
-__device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, float& t_out) {
+__device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, float& t_out,
+                                           const uint32_t* blocks = nullptr) {
     float tb = __int_as_float(0x7f800000);  // +inf
     int best = -1;
     const int n = sc.hdr->ns_pad;
@@ -161,8 +165,17 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
                 for (int i0 = 0; i0 < m; i0 += kPad) closest_block(sc.chunk + i0, c0 + i0, rp, tb, best);
             }
         } else {
+            const int nb = n / kPad;
 #pragma unroll 1
-            for (int i0 = 0; i0 < n; i0 += kPad) closest_block(sc.geo + i0, i0, rp, tb, best);
+            for (int w0 = 0; w0 < nb; w0 += 32) {
+                uint32_t m = blocks ? blocks[w0 >> 5] : (nb - w0 >= 32 ? 0xffffffffu : (1u << (nb - w0)) - 1u);
+#pragma unroll 1
+                while (m) {
+                    const int i0 = (w0 + __ffs(m) - 1) * kPad;
+                    m &= m - 1u;
+                    closest_block(sc.geo + i0, i0, rp, tb, best);
+                }
+            }
         }
     }
     const SceneHdr& h = *sc.hdr;
@@ -285,10 +298,11 @@ struct SegFilt {  // V^ of a segment in both halves
 // the necessary condition kappa^2 |oc|^2 - t^2 < rho^2 + 2 rho sigma |t|.  The pass
 // evaluates h = t^2 + 2 rho sigma |t| + rho^2 - (kappa^2 - 2^-16) |oc|^2 per sphere
 // pair (t: 3 packed FMAs, h: 3) and calls a pair clear when h < 0 in both halves and
-// |oc|^2 < 2^100.  Error budget (u = 2^-24): the FP32 axis is within 6u of unit length
-// and direction, so the computed t is within 10u |oc| of the exact projection; t^2,
-// the |t| term, |oc|^2 and the three roundings of h add at most 50u |oc|^2 + 20u rho^2,
-// below the 2^-16 |oc|^2 taken off kappa^2 and the 2^-14 rho^2 added to r_max^2.
+// |oc|^2 < 2^100.  Error budget (u = 2^-24): the FP32 axis is within 8u per component
+// of a unit vector (cone_unit), so the computed t is within 17u |oc| of the exact
+// projection; t^2, the |t| term, |oc|^2 and the three roundings of h add at most
+// 75u |oc|^2 + 25u rho^2, below the 2^-16 |oc|^2 (256u) taken off kappa^2 and the
+// 2^-14 rho^2 added to r_max^2.
 // NaN (canonical, positive) and +inf never clear.  A warp keeps one bit per block of
 // kPad spheres, set when some lane's cone is not clear of some pair of the block.  A
 // group whose every segment belongs to the cone's light, each V^ checked to satisfy
@@ -311,26 +325,38 @@ constexpr int kConeWords = 16;                        // bits per warp: 32 * kCo
 // 6.91, 7.32, 7.51 ms.
 constexpr int kConeGroup = 4;
 constexpr int kConeMaxPad = 32 * kConeWords * kPad;   // larger tables take no pre-pass
-__shared__ uint32_t s_cone[(kSegStride / 32) * kConeWords];
+__shared__ uint32_t s_cone[(kSegStride / 32) * 2 * kConeWords];  // per warp: sampled light, point lights
 __shared__ unsigned s_r2max;
 
 // rho^2 of the pre-pass: the largest r^2 of the staged table times (1 + 2^-14) (pad
 // entries, -r^2 = +1, fall out), or 0 (no pre-pass) for tables of more than
-// kConeMaxPad entries or when it leaves (0, 2^60].  Every thread of the CTA calls.
-__device__ __forceinline__ float staged_cone_r2(const float4* geo, int ns_pad) {
+// kConeMaxPad entries or when it leaves (0, 2^60]; and a bound on the centres' |c|
+// (for the primary rays' cull).  Every thread of the CTA calls.
+__shared__ unsigned s_c2max;
+__device__ __forceinline__ void staged_cone(const float4* geo, int ns_pad, StagedScene& sc) {
     const int tid = threadIdx.x + blockDim.x * threadIdx.y, nth = blockDim.x * blockDim.y;
-    if (tid == 0) s_r2max = 0u;
+    if (tid == 0) {
+        s_r2max = 0u;
+        s_c2max = 0u;
+    }
     __syncthreads();
-    float m = 0.0f;
+    float m = 0.0f, c2 = 0.0f;
     for (int q = tid; q < ns_pad / 2; q += nth) {
-        const float4 B = geo[2 * q + 1];
+        const float4 A = geo[2 * q], B = geo[2 * q + 1];
         m = fmaxf(m, fmaxf(-B.z, -B.w));
+        c2 = fmaxf(c2, fmaxf(fmaf(A.x, A.x, fmaf(A.z, A.z, B.x * B.x)), fmaf(A.y, A.y, fmaf(A.w, A.w, B.y * B.y))));
     }
     if (m > 0.0f) atomicMax(&s_r2max, __float_as_uint(m));  // non-negative floats order as their bits
+    if (c2 > 0.0f) atomicMax(&s_c2max, __float_as_uint(c2));
     __syncthreads();
     const float r2 = __uint_as_float(s_r2max) * (1.0f + 0x1p-14f);
-    return (ns_pad <= kConeMaxPad && r2 > 0.0f && r2 <= 0x1p60f) ? r2 : 0.0f;
+    sc.cone_r2 = (ns_pad <= kConeMaxPad && r2 > 0.0f && r2 <= 0x1p60f) ? r2 : 0.0f;
+    sc.cone_cmax = sqrtf(__uint_as_float(s_c2max)) * (1.0f + 0x1p-20f);  // +inf when |c|^2 overflows
 }
+
+// Unit vector for the cones' axes: rsqrtf (within 2 ulp) instead of the correctly
+// rounded root; every bound below allows 8u per component for it.
+__device__ __forceinline__ f3 cone_unit(f3 a) { return scl(a, rsqrtf(dot(a, a))); }
 
 // True when the cone (apex o via o2, axis ax, c0 = kappa^2 - 2^-16, tw = 2 rho sigma,
 // r2 = rho^2) is clear of every pair of the block of kPad spheres at g.
@@ -398,6 +424,115 @@ __device__ __noinline__ void cone_pass(const float4* __restrict__ geo, int n, un
         if (leader) cw[w0 >> 5] = word;
     }
     __syncwarp(mask);
+}
+
+// Closest-hit cull for the rays of the lanes in `mask` (origin o, direction d each).
+// The closest-hit test finds a root only where its computed m = |c x d - o x d|^2 -
+// r^2 is negative: with -(o x d) rounded once per component and two FMAs per
+// component, the computed vector is within 7u (|c| + |o|) of the exact one, so m < 0
+// needs a line distance below r (1 + 7u) + 9u (|c| + |o|) <= r_max + 2^-16 (c_max +
+// |o|).  One cone holds every lane's line: apex p0 = the first lane's origin, axis a
+// along the sum of the first and last lane's directions (cone_unit), kappa the
+// warp's minimum of a.d less 2^-18 (the roundings of a.d stay below 25u); a lane's
+// line lies within |o - p0| of it, so rho = (r_max + 2^-16 (c_max + max |o|) + max |o
+// - p0|) (1 + 2^-16) bounds the distance of every sphere with a root.  The blocks
+// are split over the lanes and tested once against that cone (cone_block_clear,
+// whose slack covers the rounding of c - p0); bit b of cw is set for every block the
+// cone does not clear.  A skipped block holds no sphere with a root, so the closest
+// hit (strict <, index order over the rest) is unchanged.  For a warp of primary
+// rays p0 is every lane's origin (the camera) and the cone is the patch's view
+// frustum.  Returns false, writing nothing, when the rays do not fit a cone of
+// half-angle below 60 degrees.
+__device__ __noinline__ bool ray_cull(const float4* __restrict__ geo, int n, unsigned mask, f3 o, f3 d,
+                                      float r_max, float c_max, uint32_t* cw) {
+    const int lane = threadIdx.x & 31;
+    const int lo = __ffs(mask) - 1, hi = 31 - __clz(mask);
+    const f3 dl = mk3(__shfl_sync(mask, d.x, lo), __shfl_sync(mask, d.y, lo), __shfl_sync(mask, d.z, lo));
+    const f3 dh = mk3(__shfl_sync(mask, d.x, hi), __shfl_sync(mask, d.y, hi), __shfl_sync(mask, d.z, hi));
+    const f3 p0 = mk3(__shfl_sync(mask, o.x, lo), __shfl_sync(mask, o.y, lo), __shfl_sync(mask, o.z, lo));
+    const f3 a = cone_unit(add(dl, dh));
+    const float k = dot(a, d);
+    const f3 dp = sub(o, p0);
+    // warp minimum / maxima (non-negative floats order as their bits)
+    const float kw = __uint_as_float(__reduce_min_sync(mask, __float_as_uint(k >= 0.5f ? k : 0.0f))) - 0x1p-18f;
+    const float om = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(sqrtf(dot(o, o)))));
+    const float dm = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(sqrtf(dot(dp, dp)))));
+    const float rho = (r_max + 0x1p-16f * (c_max + om) + dm) * (1.0f + 0x1p-16f);
+    if (!(kw >= 0.5f && rho <= 0x1p30f)) return false;
+    const float sw = sqrtf(fmaxf(fmaf(-kw, kw, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
+    const int nb = n / kPad;
+    const int rank = __popc(mask & ((1u << lane) - 1u)), cnt = __popc(mask);
+    for (int w = rank; w < (nb + 31) / 32; w += cnt) cw[w] = 0u;
+    __syncwarp(mask);
+    const RayPair o2 = ray_pair(p0);
+    const float2 ax = dup2(a.x), ay = dup2(a.y), az = dup2(a.z);
+    const float2 c0 = dup2(-fmaf(kw, kw, -0x1p-16f)), tw = dup2(2.0f * rho * sw);
+    const float2 r2 = dup2(rho * rho * (1.0f + 0x1p-15f));
+#pragma unroll 1
+    for (int b = rank; b < nb; b += cnt)
+        if (!cone_block_clear(geo + (size_t)b * kPad, o2, ax, ay, az, c0, tw, r2)) atomicOr(&cw[b >> 5], 1u << (b & 31));
+    __syncwarp(mask);
+    return true;
+}
+
+// Point lights.  A segment of point light L starts at its lane's shadow origin po and
+// ends at po + V = L + E (E: the origin's offset eps n, plus roundings), so it lies
+// within |E| of the segment from po to L, which lies in any cone with apex L that
+// holds the direction to po.  For each light l of `lights` the lanes whose group
+// holds l (bit l of gl) form one cone: axis from L to the first such lane's po, kappa
+// the lanes' minimum cosine less 2^-18, rho_l = (rho + max |E| + 2^-16 (|L| + max |po
+// - L|)) (1 + 2^-15), the 2^-16 term covering the roundings of E and of c - L.  The
+// blocks are split over the lanes and tested once per light (cone_block_clear); cw
+// receives the union of the blocks no cone clears.  Returns false (visit every
+// block) when some light's lanes do not fit a cone below 60 degrees.
+__device__ __noinline__ bool point_pass(const float4* __restrict__ geo, int n, unsigned mask, const SceneHdr& h, f3 p,
+                                        f3 p_lo, f3 po, uint32_t gl, unsigned lights, float rho, uint32_t* cw) {
+    const int lane = threadIdx.x & 31;
+    const int nb = n / kPad;
+    const int rank = __popc(mask & ((1u << lane) - 1u)), cnt = __popc(mask);
+    for (int w = rank; w < (nb + 31) / 32; w += cnt) cw[w] = 0u;
+    __syncwarp(mask);
+    bool ok = true;
+    unsigned rest = lights;
+#pragma unroll 1
+    while (rest) {
+        const int l = __ffs(rest) - 1;
+        rest &= rest - 1u;
+        const f3 L = xyz(h.light_p[l]);
+        const bool has = (gl >> l) & 1u;
+        const int ld = __ffs(__ballot_sync(mask, has)) - 1;
+        const f3 dir = has ? cone_unit(sub(po, L)) : mk3(0.f, 0.f, 0.f);
+        const f3 a = mk3(__shfl_sync(mask, dir.x, ld), __shfl_sync(mask, dir.y, ld), __shfl_sync(mask, dir.z, ld));
+        float k = 1.0f, e = 0.0f, dd = 0.0f;
+        if (has) {
+            k = dot(a, dir);
+            k = k >= 0.5f ? k : 0.0f;  // NaN: 0
+            const f3 E = sub(add(po, sub(sub(L, p), p_lo)), L);  // po + V - L, V as the set-up forms it
+            e = sqrtf(dot(E, E));
+            const f3 D = sub(po, L);
+            dd = sqrtf(dot(D, D));
+        }
+        // warp minimum / maxima (non-negative floats order as their bits)
+        const float kw = __uint_as_float(__reduce_min_sync(mask, __float_as_uint(k))) - 0x1p-18f;
+        const float em = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(e)));
+        const float dm = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(dd)));
+        const float rl = (rho + em + 0x1p-16f * (sqrtf(dot(L, L)) + dm)) * (1.0f + 0x1p-15f);
+        if (!(kw >= 0.5f && rl <= 0x1p30f)) {
+            ok = false;
+            break;
+        }
+        const float sw = sqrtf(fmaxf(fmaf(-kw, kw, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
+        const RayPair o2 = ray_pair(L);
+        const float2 ax = dup2(a.x), ay = dup2(a.y), az = dup2(a.z);
+        const float2 c0 = dup2(-fmaf(kw, kw, -0x1p-16f)), tw = dup2(2.0f * rl * sw);
+        const float2 r2 = dup2(rl * rl * (1.0f + 0x1p-15f));
+#pragma unroll 1
+        for (int b = rank; b < nb; b += cnt)
+            if (!cone_block_clear(geo + (size_t)b * kPad, o2, ax, ay, az, c0, tw, r2))
+                atomicOr(&cw[b >> 5], 1u << (b & 31));
+    }
+    __syncwarp(mask);
+    return ok;
 }
 
 // Segment test of pair q (spheres 2q, 2q + 1 of geo) against the R segments, the
@@ -809,8 +944,8 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
     if (lc >= 0 && sc.cone_r2 > 0.0f) {
         const float4 Lp = h.light_p[lc], Ls = h.light_s[lc];
         const f3 Lv = sub(sub(xyz(Lp), p), p_lo);
-        float dist;
-        ax = normalize_rn(Lv, &dist);
+        const float ri = rsqrtf(dot(Lv, Lv));
+        ax = scl(Lv, ri);
         if (Ls.x > 0.0f) {
             const float hs = 0.5f * Ls.x;
             kap = 1.0f;
@@ -820,13 +955,13 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 kap = fminf(kap, dot(ax, cv) * rsqrtf(dot(cv, cv)));
             }
         } else {
-            const float sr = Ls.y / dist;
+            const float sr = Ls.y * ri * (1.0f + 0x1p-20f);  // >= R / dist
             kap = sqrtf(fmaxf(fmaf(-sr, sr, 1.0f), 0.0f));
         }
         kap -= 0x1p-17f;
         cone_ok = kap >= 0.5f;  // NaN: false
     }
-    uint32_t* cw = s_cone + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5) * kConeWords;
+    uint32_t* cw = s_cone + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5) * 2 * kConeWords;
     unsigned cm = __ballot_sync(mask, cone_ok);
     if (cm) {
         // the warp's cone: apex and axis of the first lane with a cone; lanes whose
@@ -874,6 +1009,8 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         uint32_t blocked = 0;
         bool ok = true;
         bool pure = cone_ok || kr == 0;  // every segment of the group inside the cone of light lc
+        bool allpt = true;               // every segment of the group to a point light
+        uint32_t gl = 0;                 // the group's lights
 #pragma unroll 1
         for (int j = 0; j < (R <= kConeGroup ? kConeGroup : R); ++j) {  // slots read by the instance below
             f3 W = mk3(0.f, 0.f, 0.f), nv = mk3(0.f, 0.f, 0.f), vn = mk3(0.f, 0.f, 0.f);
@@ -883,6 +1020,8 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 const float4 Ls = h.light_s[l];
                 const int nr = rays_of_light(fr, Ls);
                 pure = pure && l == lc;
+                allpt = allpt && Ls.x == 0.0f && Ls.y == 0.0f;
+                gl |= 1u << l;
                 if (Ls.y > 0.0f && lf_l != l) {
                     lf = light_frame(p, Lp);
                     lf_l = l;
@@ -924,6 +1063,11 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         }
         const bool exact_only = !__all_sync(mask, ok);
         const uint32_t* cone = cone_any && __all_sync(mask, pure) ? cw : nullptr;
+        if (!cone && sc.cone_r2 > 0.0f && __all_sync(mask, allpt)) {
+            const unsigned gu = __reduce_or_sync(mask, gl);
+            if (gu && point_pass(sc.geo, h.ns_pad, mask, h, p, p_lo, po, gl, gu, sqrtf(sc.cone_r2), cw + kConeWords))
+                cone = cw + kConeWords;
+        }
         static_assert(kFiltGroup >= 4 && kFiltGroup <= 8 && kConeGroup == 4, "dispatch below");
         constexpr int G = kFiltGroup;
         const int np = h.ns_pad;
@@ -1163,7 +1307,15 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
 #pragma unroll 1
     for (; k <= fr.D; ++k) {
         float t;
-        const int id = closest_hit<CH, ACC>(sc, o, d, t);
+        const uint32_t* cull = nullptr;
+        if constexpr (!CH && !ACC && FM == 1) {
+            // the blocks the warp's ray lines can reach (a view frustum for primary rays)
+            if (sc.cone_r2 > 0.0f) {
+                uint32_t* cw = s_cone + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5) * 2 * kConeWords;
+                if (ray_cull(sc.geo, h.ns_pad, __activemask(), o, d, sqrtf(sc.cone_r2), sc.cone_cmax, cw)) cull = cw;
+            }
+        }
+        const int id = closest_hit<CH, ACC>(sc, o, d, t, cull);
         if (HITREC) {
             float* rec = hr + (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
             rec[0] = __int_as_float(id);
