@@ -101,7 +101,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_kernel(const SceneView sv, cons
     StagedScene sc{hdr, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)warp * kChunk : nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (FM == 1 && !CH) sc.cone_r2 = staged_cone_r2(tab, hdr->ns_pad);
+    if constexpr (FM == 1 && !CH) staged_cone(tab, hdr->ns_pad, sc);
 
     const int wpr = block_x >> 3;
     const int x = fr.rx0 + blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
@@ -156,7 +156,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_p0_kernel(const SceneView sv, c
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (FM == 1) sc.cone_r2 = staged_cone_r2(sc.geo, hdr->ns_pad);
+    if constexpr (FM == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
     WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
     const PathQueue q1 = ws_queue(ws, cap, 1);
     const int wpr = block_x >> 3, wpt = (block_x * block_y) >> 5;
@@ -204,7 +204,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (FM == 1) sc.cone_r2 = staged_cone_r2(sc.geo, hdr->ns_pad);
+    if constexpr (FM == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
     const PathQueue cur = ws_queue(ws, cap, k);
     const PathQueue nxt = ws_queue(ws, cap, k + 1);
     if constexpr (FM == 1) {
