@@ -511,6 +511,7 @@ Frame make_frame(const rt_scene* s, const rt_camera* c, const rt_render_params* 
     const int g = (int)std::lround(std::sqrt((double)p->shadow_samples));
     fr.sample_g = g > 0 ? g : 1;
     fr.sample_g_inv = (float)(1.0 / (double)fr.sample_g);
+    fr.sample_g_magic = (uint32_t)(((1u << 22) + (uint32_t)fr.sample_g - 1u) / (uint32_t)fr.sample_g);
     (void)s;
     return fr;
 }

@@ -137,6 +137,7 @@ struct Frame {
     uint32_t key0, key1;     // Philox key = seed
     float sample_g_inv;      // 1 / g for the g x g stratified grid
     int sample_g;
+    uint32_t sample_g_magic; // ceil(2^22 / g): s div g = umulhi(s * 2^10, it) for s < 2^10, g <= 32
     float refl_inv_max;      // > 0: reflection ratio = min(spec_exp * refl_inv_max, 1)
 };
 

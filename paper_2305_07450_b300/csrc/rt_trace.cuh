@@ -750,7 +750,11 @@ __device__ __forceinline__ f3 sample_point(const Frame& fr, uint32_t pix, int k,
         const float xi1 = u24((s & 1) ? w.z : w.x);
         const float xi2 = u24((s & 1) ? w.w : w.y);
         const int g = fr.sample_g;
-        const int i = s % g, j = s / g;
+        // j = s div g by a multiply-high: with M = ceil(2^22 / g) the product s 2^10 M /
+        // 2^32 exceeds s / g by less than 2^-12 < 1 / g (s < 2^10, g <= 32), so its floor
+        // is s div g (checked for every such s and g)
+        const int j = (int)__umulhi((uint32_t)s << 10, fr.sample_g_magic);
+        const int i = s - j * g;
         const float a = Ls.x, ginv = fr.sample_g_inv;
         return mk3(Lp.x + (((float)i + xi1) * ginv - 0.5f) * a, Lp.y, Lp.z + (((float)j + xi2) * ginv - 0.5f) * a);
     }
