@@ -363,8 +363,13 @@ __device__ __forceinline__ f3 cone_unit(f3 a) { return scl(a, rsqrtf(dot(a, a)))
 __device__ __forceinline__ bool cone_block_clear(const float4* __restrict__ g, const RayPair& o2, float2 axx,
                                                  float2 axy, float2 axz, float2 nc0, float2 tw, float2 r2) {
     uint32_t clr = 0xffffffffu;
+    // each lane starts at pair (lane mod 4): lanes testing different blocks (128 bytes
+    // apart) would otherwise load from the same shared-memory banks
+    static_assert(((kPad / 2) & (kPad / 2 - 1)) == 0, "pairs per block: a power of two");
+    const int rot = threadIdx.x & (kPad / 2 - 1);
 #pragma unroll
-    for (int q = 0; q < kPad / 2; ++q) {
+    for (int qq = 0; qq < kPad / 2; ++qq) {
+        const int q = (qq + rot) & (kPad / 2 - 1);
         const float4 A = g[2 * q], B = g[2 * q + 1];
         const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
         const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
