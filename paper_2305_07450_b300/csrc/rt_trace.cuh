@@ -264,21 +264,25 @@ __device__ __forceinline__ bool occluded_block(const float4* __restrict__ geo, u
 // |oc|^2 exceeds 2^100 is flagged too, and a group whose S leaves [2^-60, 2^100]
 // for some lane takes the segment test throughout.  The flags are kept as the AND
 // of sign bits ("certainly clear" = every value negative), so NaN and +inf count
-// as "maybe".  W and -V of each segment wait in shared memory (6 floats per segment
-// and thread, written once per group) for the pairs that need the segment test.
+// as "maybe".  W, -V and V^ of each segment wait in shared memory (9 floats per
+// segment and thread, written once per group): V^ for the filter, W and -V for the
+// pairs that need the segment test.
 constexpr int kFilterMinPad = 128;  // smaller sphere tables keep the segment test alone
-// Segments traced together by the filtered path: |oc|^2 and the pair's flags are
-// shared by the group, so larger groups pay them fewer times per hit (a 4K hit's
-// 19 segments go as 7, 7, 5).  Measured on B300 at 128 registers, 4K queued frame:
-// 9.99 / 9.79 / 9.64 / 9.48 / 9.64 ms for groups of 4 / 5 / 6 / 7 / 8.
-constexpr int kFiltGroup = 7;
+// Segments traced together by the filtered path.  Without the cone pre-pass larger
+// groups paid |oc|^2 and the pair's flags fewer times per hit (4K queued frame:
+// 9.99 / 9.79 / 9.64 / 9.48 / 9.64 ms for groups of 4 / 5 / 6 / 7 / 8); with the
+// pre-pass and the warp cones a group visits a few blocks, and groups of 4 let each
+// slot keep its unit vector in shared memory beside W and -V (9 floats per slot and
+// thread, 36 KB per CTA): 4K frame 5.36 -> 5.07 ms against groups of 7 with the unit
+// vectors in a local array.
+constexpr int kFiltGroup = 4;
 constexpr float kFiltK1 = 1.0f - 64.0f / 16777216.0f;
 constexpr float kFiltK2 = 1.0f + 64.0f / 16777216.0f;
 constexpr int kSegStride = 256;  // threads per CTA at most (the launch shapes allow 256)
 
 // One array per kernel (namespace scope): every instantiation of the shadow test
 // shares it.
-__shared__ float s_seg[6 * kFiltGroup * kSegStride];
+__shared__ float s_seg[9 * kFiltGroup * kSegStride];
 
 struct SegFilt {  // V^ of a segment in both halves
     float2 vx, vy, vz;
@@ -542,7 +546,7 @@ __device__ __noinline__ bool point_pass(const float4* __restrict__ geo, int n, u
 
 // Segment test of pair q (spheres 2q, 2q + 1 of geo) against the R segments, the
 // operations of occluded_block; W and -V from shared memory (seg[k * kSegStride],
-// k = 6 r + (0..2: W, 3..5: -V)).
+// k = 9 r + (0..2: W, 3..5: -V); 6..8 hold V^).
 template <int R>
 __device__ __forceinline__ void pair_exact(const float4* __restrict__ geo, int q, const RayPair& o2,
                                            const float* seg, uint32_t (&acc)[kFiltGroup]) {
@@ -553,7 +557,7 @@ __device__ __forceinline__ void pair_exact(const float4* __restrict__ geo, int q
     const float2 nr = make_float2(B.z, B.w);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const float* g = seg + 6 * r * kSegStride;
+        const float* g = seg + 9 * r * kSegStride;
         const float wx = g[0], wy = g[kSegStride], wz = g[2 * kSegStride];
         const float2 t = fma2(ocy, dup2(wy), mul2(ocz, dup2(wz)));
         const float2 u = make_float2(fma_sat(ocx.x, wx, t.x), fma_sat(ocx.y, wx, t.y));
@@ -610,23 +614,24 @@ __device__ __forceinline__ bool occluded_block_filtered(const float4* __restrict
 // The filtered sphere loop of one group, out of line: inlined into the shading
 // code its registers and the caller's live state spilled inside the sphere loop
 // (ncu: 2e8 local loads and stores per 1080p launch); called, the caller's state is
-// saved once per group.  vh[3 r .. 3 r + 2] = V^ of segment r (zero for segments
-// already blocked); blocked_in / the result: bit r = segment r blocked.  The
-// caller has written W and -V to seg (shared memory).  exact_only: the segment
+// saved once per group.  The caller has written W, -V and V^ of segment r to slot r
+// of seg (shared memory; V^ zero for segments already blocked); blocked_in / the
+// result: bit r = segment r blocked.  exact_only: the segment
 // test for every pair (a group for which the filter's bound is not established).
 // cone: the warp's block bits of the cone pre-pass (only the blocks whose bit is set
 // are visited), or null (every block).
 template <int R>
 __device__ __noinline__ uint32_t occluded_filtered(const float4* __restrict__ geo, int n, unsigned mask, f3 o,
-                                                   const float* __restrict__ vh, uint32_t blocked_in,
-                                                   const float* seg, bool exact_only, const uint32_t* cone) {
+                                                   uint32_t blocked_in, const float* seg, bool exact_only,
+                                                   const uint32_t* cone) {
     const RayPair o2 = ray_pair(o);
     SegFilt sf[kFiltGroup];
     uint32_t acc[kFiltGroup];
 #pragma unroll
     for (int r = 0; r < kFiltGroup; ++r) {
         acc[r] = (blocked_in >> r) & 1u ? 0x80000000u : 0u;
-        sf[r] = r < R ? SegFilt{dup2(vh[3 * r]), dup2(vh[3 * r + 1]), dup2(vh[3 * r + 2])}
+        sf[r] = r < R ? SegFilt{dup2(seg[(9 * r + 6) * kSegStride]), dup2(seg[(9 * r + 7) * kSegStride]),
+                                dup2(seg[(9 * r + 8) * kSegStride])}
                       : SegFilt{dup2(0.f), dup2(0.f), dup2(0.f)};
     }
     if (exact_only) {  // the filter's bound does not hold for some lane: the segment test throughout
@@ -1014,14 +1019,13 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         const int kr = min(cone_ok && done >= before_lc ? kConeGroup : kFiltGroup, lim - done);
         const int R = (int)__reduce_max_sync(mask, (unsigned)kr);
         if (R == 0) break;
-        float vh[3 * kFiltGroup];
         uint32_t blocked = 0;
         bool ok = true;
         bool pure = cone_ok || kr == 0;  // every segment of the group inside the cone of light lc
         bool allpt = true;               // every segment of the group to a point light
         uint32_t gl = 0;                 // the group's lights
 #pragma unroll 1
-        for (int j = 0; j < (R <= kConeGroup ? kConeGroup : R); ++j) {  // slots read by the instance below
+        for (int j = 0; j < kFiltGroup; ++j) {  // every slot: the instance below reads kFiltGroup
             f3 W = mk3(0.f, 0.f, 0.f), nv = mk3(0.f, 0.f, 0.f), vn = mk3(0.f, 0.f, 0.f);
             bool occj = true;
             if (j < kr) {
@@ -1059,10 +1063,10 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 }
             }
             blocked |= occj ? (1u << j) : 0u;
-            vh[3 * j] = vn.x;
-            vh[3 * j + 1] = vn.y;
-            vh[3 * j + 2] = vn.z;
-            float* g = seg + 6 * j * kSegStride;
+            float* g = seg + 9 * j * kSegStride;
+            g[6 * kSegStride] = vn.x;
+            g[7 * kSegStride] = vn.y;
+            g[8 * kSegStride] = vn.z;
             g[0] = W.x;
             g[kSegStride] = W.y;
             g[2 * kSegStride] = W.z;
@@ -1077,14 +1081,8 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
             if (gu && point_pass(sc.geo, h.ns_pad, mask, h, p, p_lo, po, gl, gu, sqrtf(sc.cone_r2), cw + kConeWords))
                 cone = cw + kConeWords;
         }
-        static_assert(kFiltGroup >= 4 && kFiltGroup <= 8 && kConeGroup == 4, "dispatch below");
-        constexpr int G = kFiltGroup;
-        const int np = h.ns_pad;
-        if (R <= kConeGroup) blocked = occluded_filtered<kConeGroup>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
-        else if (R == 5) blocked = occluded_filtered<(G < 5 ? G : 5)>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
-        else if (R == 6) blocked = occluded_filtered<(G < 6 ? G : 6)>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
-        else if (R == 7) blocked = occluded_filtered<(G < 7 ? G : 7)>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
-        else blocked = occluded_filtered<G>(sc.geo, np, mask, po, vh, blocked, seg, exact_only, cone);
+        static_assert(kFiltGroup == 4 && kConeGroup == 4, "one instance: every group has at most 4 segments");
+        blocked = occluded_filtered<kFiltGroup>(sc.geo, h.ns_pad, mask, po, blocked, seg, exact_only, cone);
         // attribute the results to their lights in the same order
 #pragma unroll 1
         for (int j = 0; j < kr; ++j) {
@@ -1576,10 +1574,9 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
                 vn = scl(nv, -rsqrtf(S));
             }
         }
-        float vh[3 * kFiltGroup];
-        vh[0] = vn.x;
-        vh[1] = vn.y;
-        vh[2] = vn.z;
+        seg[6 * kSegStride] = vn.x;
+        seg[7 * kSegStride] = vn.y;
+        seg[8 * kSegStride] = vn.z;
         seg[0] = W.x;
         seg[kSegStride] = W.y;
         seg[2 * kSegStride] = W.z;
@@ -1587,7 +1584,7 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
         seg[4 * kSegStride] = nv.y;
         seg[5 * kSegStride] = nv.z;
         const bool exact_only = !__all_sync(0xffffffffu, ok);
-        const uint32_t blocked = occluded_filtered<1>(sc.geo, h.ns_pad, 0xffffffffu, po, vh, occj ? 1u : 0u, seg,
+        const uint32_t blocked = occluded_filtered<1>(sc.geo, h.ns_pad, 0xffffffffu, po, occj ? 1u : 0u, seg,
                                                       exact_only, nullptr);
         const bool vis = valid && !(blocked & 1u);
 #pragma unroll
