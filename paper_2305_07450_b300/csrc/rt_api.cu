@@ -560,7 +560,7 @@ int max_smem_optin() {
 
 // The whole geometry table is staged unless it does not fit (or the tiled loop is
 // forced with staging = 3).
-constexpr size_t kStaticSmemReserve = 4 * 1024 + 9 * 4 * kSegStride * kFiltGroup;
+constexpr size_t kStaticSmemReserve = 12 * 1024 + 9 * 4 * kSegStride * kFiltGroup;
 size_t stage_smem_bytes(bool chunked, int ns_pad, int nwarps) {
     return chunked ? sizeof(SceneHdr) + (size_t)nwarps * kChunk * 16 : sizeof(SceneHdr) + (size_t)ns_pad * 16;
 }

@@ -396,9 +396,10 @@ __device__ __forceinline__ bool cone_block_clear(const float4* __restrict__ g, c
 // its radius rho plus the farthest lane apex): only the blocks it does not clear
 // are tested against the lanes' own cones.  Out of line: the shading code keeps its
 // registers.
-__device__ __noinline__ void cone_pass(const float4* __restrict__ geo, int n, unsigned mask, f3 o, f3 ax, float c0,
-                                       float twors, float rho2, bool use, uint32_t* cw, f3 p0, f3 aw, float wc0,
-                                       float wtw, float wr2, bool coarse) {
+// Returns this lane's own bits of blocks 0..31 (its cone alone; for item_groups).
+__device__ __noinline__ uint32_t cone_pass(const float4* __restrict__ geo, int n, unsigned mask, f3 o, f3 ax,
+                                           float c0, float twors, float rho2, bool use, uint32_t* cw, f3 p0, f3 aw,
+                                           float wc0, float wtw, float wr2, bool coarse) {
     const int lane = threadIdx.x & 31;
     const int nb = n / kPad;
     const bool leader = lane == __ffs(mask) - 1;
@@ -418,6 +419,7 @@ __device__ __noinline__ void cone_pass(const float4* __restrict__ geo, int n, un
     const RayPair o2 = ray_pair(o);
     const float2 axx = dup2(ax.x), axy = dup2(ax.y), axz = dup2(ax.z);
     const float2 nc0 = dup2(-c0), tw = dup2(twors), r2 = dup2(rho2);
+    uint32_t own = 0;
 #pragma unroll 1
     for (int w0 = 0; w0 < nb; w0 += 32) {
         uint32_t m = coarse ? cw[w0 >> 5] : (nb - w0 >= 32 ? 0xffffffffu : (1u << (nb - w0)) - 1u);
@@ -426,13 +428,15 @@ __device__ __noinline__ void cone_pass(const float4* __restrict__ geo, int n, un
         while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1u;
-            const bool clear = cone_block_clear(geo + (size_t)(w0 + b) * kPad, o2, axx, axy, axz, nc0, tw, r2);
-            word |= (__any_sync(mask, use && !clear) ? 1u : 0u) << b;
+            const bool need = use && !cone_block_clear(geo + (size_t)(w0 + b) * kPad, o2, axx, axy, axz, nc0, tw, r2);
+            if (w0 == 0 && need) own |= 1u << b;
+            word |= (__any_sync(mask, need) ? 1u : 0u) << b;
         }
         __syncwarp(mask);  // every lane has read the coarse word
         if (leader) cw[w0 >> 5] = word;
     }
     __syncwarp(mask);
+    return own;
 }
 
 // Closest-hit cull for the rays of the lanes in `mask` (origin o, direction d each).
@@ -611,6 +615,90 @@ __device__ __forceinline__ bool occluded_block_filtered(const float4* __restrict
     return __all_sync(mask, done);
 }
 
+// Item mode of a group (occluded_filtered with items): where the lanes' hits lie far
+// apart (queue passes), the blocks some lane's cone reaches are needed by a few lanes
+// each (ncu-side count at 4K: 5 of 32 lanes per visited block), so iterating the
+// warp's union idles most of each step.  Instead the (lane, block) pairs of the lanes'
+// own bits are numbered (warp scan of the counts) and the 32 lanes take them 32 at a
+// time: lane j tests block b for lane L's segments -- L's origin and slots read from
+// shared memory, the filter and, for the pairs it flags, the segment test, the
+// operations of occluded_block_filtered -- and ORs the blocked segments into L's
+// result word.  Every pair of every own block is tested (no early exit), and a
+// verdict is an OR over blocks, so the result equals the union loop's bit for bit.
+// Lanes whose segments are all blocked already contribute no pairs.  A full warp calls.
+__shared__ float s_it_o[3 * kSegStride];
+__shared__ int s_it_start[kSegStride];
+__shared__ uint32_t s_it_own[kSegStride], s_it_res[kSegStride];
+template <int R>
+__device__ __forceinline__ uint32_t item_groups(const float4* __restrict__ geo, f3 o, uint32_t blocked_in,
+                                                const float* seg, uint32_t own) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wb = tid - lane;
+    const uint32_t rmask = (1u << R) - 1u;
+    const uint32_t mine = (blocked_in & rmask) == rmask ? 0u : own;
+    const int cnt = __popc(mine);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    s_it_start[tid] = incl - cnt;
+    s_it_own[tid] = mine;
+    s_it_o[tid] = o.x;
+    s_it_o[kSegStride + tid] = o.y;
+    s_it_o[2 * kSegStride + tid] = o.z;
+    s_it_res[tid] = blocked_in & rmask;
+    __syncwarp();
+    const float* seg0 = seg - lane;  // slot base of the warp's first lane
+#pragma unroll 1
+    for (int i = lane; i < total; i += 32) {
+        // owner: the last lane whose first item is at most i (counts of zero share a start)
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (s_it_start[wb + L + step] <= i) L += step;
+        uint32_t x = s_it_own[wb + L];
+        for (int k = i - s_it_start[wb + L]; k > 0; --k) x &= x - 1u;
+        const float4* g = geo + (size_t)(__ffs(x) - 1) * kPad;
+        const float* segL = seg0 + L;
+        const RayPair o2 = ray_pair(mk3(s_it_o[wb + L], s_it_o[kSegStride + wb + L], s_it_o[2 * kSegStride + wb + L]));
+        SegFilt sf[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            sf[r] = SegFilt{dup2(segL[(9 * r + 6) * kSegStride]), dup2(segL[(9 * r + 7) * kSegStride]),
+                            dup2(segL[(9 * r + 8) * kSegStride])};
+        uint32_t acc[kFiltGroup];
+#pragma unroll
+        for (int r = 0; r < kFiltGroup; ++r) acc[r] = 0u;
+#pragma unroll 1
+        for (int q = 0; q < kPad / 2; ++q) {
+            const float4 A = g[2 * q], B = g[2 * q + 1];
+            const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
+            const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
+            const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
+            const float2 oc2 = fma2(ocx, ocx, fma2(ocy, ocy, mul2(ocz, ocz)));
+            const float2 c = fma2(oc2, dup2(-kFiltK1), mul2(make_float2(B.z, B.w), dup2(-kFiltK2)));
+            const float2 big = add2(oc2, dup2(-0x1p100f));
+            uint32_t clear = __float_as_uint(big.x) & __float_as_uint(big.y);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 t = fma2(ocx, sf[r].vx, fma2(ocy, sf[r].vy, mul2(ocz, sf[r].vz)));
+                const float2 gg = fma2(t, t, c);
+                clear &= __float_as_uint(gg.x) & __float_as_uint(gg.y);
+            }
+            if (!(clear >> 31)) pair_exact<R>(g, q, o2, segL, acc);
+        }
+        uint32_t bits = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) bits |= (acc[r] >> 31) << r;
+        if (bits) atomicOr(&s_it_res[wb + L], bits);
+    }
+    __syncwarp();
+    return s_it_res[tid];
+}
+
 // The filtered sphere loop of one group, out of line: inlined into the shading
 // code its registers and the caller's live state spilled inside the sphere loop
 // (ncu: 2e8 local loads and stores per 1080p launch); called, the caller's state is
@@ -619,11 +707,13 @@ __device__ __forceinline__ bool occluded_block_filtered(const float4* __restrict
 // result: bit r = segment r blocked.  exact_only: the segment
 // test for every pair (a group for which the filter's bound is not established).
 // cone: the warp's block bits of the cone pre-pass (only the blocks whose bit is set
-// are visited), or null (every block).
+// are visited), or null (every block).  items (a full warp, blocks 0..31 only): each
+// lane's own bits `own` instead of the warp's union -- see item_groups.
 template <int R>
 __device__ __noinline__ uint32_t occluded_filtered(const float4* __restrict__ geo, int n, unsigned mask, f3 o,
                                                    uint32_t blocked_in, const float* seg, bool exact_only,
-                                                   const uint32_t* cone) {
+                                                   const uint32_t* cone, uint32_t own, bool items) {
+    if (items && !exact_only) return item_groups<R>(geo, o, blocked_in, seg, own);
     const RayPair o2 = ray_pair(o);
     SegFilt sf[kFiltGroup];
     uint32_t acc[kFiltGroup];
@@ -976,6 +1066,8 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         cone_ok = kap >= 0.5f;  // NaN: false
     }
     uint32_t* cw = s_cone + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5) * 2 * kConeWords;
+    uint32_t own = 0;    // this lane's own blocks (cone_pass)
+    bool items = false;  // the cone's groups in item mode (item_groups)
     unsigned cm = __ballot_sync(mask, cone_ok);
     if (cm) {
         // the warp's cone: apex and axis of the first lane with a cone; lanes whose
@@ -1006,8 +1098,13 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         const float rw = (rho + dwm) * (1.0f + 0x1p-15f);
         const float sw = sqrtf(fmaxf(fmaf(-kwm, kwm, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
         const float sg = sa * (1.0f + 0x1p-18f);  // >= sin alpha
-        cone_pass(sc.geo, h.ns_pad, mask, po, ax, fmaf(kap, kap, -0x1p-16f), 2.0f * rho * sg, sc.cone_r2, cone_ok, cw,
-                  p0, aw, fmaf(kwm, kwm, -0x1p-16f), 2.0f * rw * sw, rw * rw * (1.0f + 0x1p-15f), coarse);
+        own = cone_pass(sc.geo, h.ns_pad, mask, po, ax, fmaf(kap, kap, -0x1p-16f), 2.0f * rho * sg, sc.cone_r2,
+                        cone_ok, cw, p0, aw, fmaf(kwm, kwm, -0x1p-16f), 2.0f * rw * sw, rw * rw * (1.0f + 0x1p-15f),
+                        coarse);
+        // item mode for the cone's groups where the lanes' own blocks are under a third
+        // of the union's steps (a full warp, at most 32 blocks)
+        if (mask == 0xffffffffu && h.ns_pad <= 32 * kPad)
+            items = 3u * __reduce_add_sync(mask, (unsigned)__popc(own)) < 32u * (unsigned)__popc(cw[0]);
     }
     const bool cone_any = cm != 0;
     const float kv = kap + 0x1p-18f;
@@ -1082,7 +1179,8 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 cone = cw + kConeWords;
         }
         static_assert(kFiltGroup == 4 && kConeGroup == 4, "one instance: every group has at most 4 segments");
-        blocked = occluded_filtered<kFiltGroup>(sc.geo, h.ns_pad, mask, po, blocked, seg, exact_only, cone);
+        blocked = occluded_filtered<kFiltGroup>(sc.geo, h.ns_pad, mask, po, blocked, seg, exact_only, cone, own,
+                                                items && cone == cw);
         // attribute the results to their lights in the same order
 #pragma unroll 1
         for (int j = 0; j < kr; ++j) {
@@ -1585,7 +1683,7 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
         seg[5 * kSegStride] = nv.z;
         const bool exact_only = !__all_sync(0xffffffffu, ok);
         const uint32_t blocked = occluded_filtered<1>(sc.geo, h.ns_pad, 0xffffffffu, po, occj ? 1u : 0u, seg,
-                                                      exact_only, nullptr);
+                                                      exact_only, nullptr, 0u, false);
         const bool vis = valid && !(blocked & 1u);
 #pragma unroll
         for (int li = 0; li < RT_MAX_LIGHTS; ++li)
