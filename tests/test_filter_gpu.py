@@ -187,3 +187,14 @@ def test_cone_with_huge_coordinates():
     sph[:5, 2] = S.f32([1e20, 1e20, -1e20, -2e20, 5e19])
     sc.spheres = sph
     assert_filter_exact(sc, cam, p)
+
+
+def test_incoherent_warps_with_an_area_light():
+    """160 spheres of reflectivity 0.9..1 packed in front of the camera, a point light
+    and a square light, bounce limit 6: the queue passes' warps hold paths from all
+    over the image (the cone groups' item mode: each lane's own blocks shared out over
+    the warp), against the tiled loop, which has neither the filter nor the cones."""
+    sc = S.random_scene(17, 160, 2, 0.6, area_lights=1, area_side=1.5)
+    sc.spheres[:, 9] = np.random.default_rng(17).uniform(0.9, 1.0, 160).astype(np.float32)
+    p = S._params(sc, width=256, height=160, max_depth=6, shadow_samples=16, out_format=S.OUT_F32, seed=17)
+    assert_filter_exact(sc, S.default_camera(0.6), p)
