@@ -2,9 +2,13 @@
 // Section 3) in FP32: primary ray, brute-force closest hit, shading with hard or
 // sampled shadows (the segment test, and in front of it for large scenes a line
 // filter that decides most sphere-segment pairs in fewer operations with the same
-// verdict), register-resident reflection loop, and the bounce queues of the queued
-// render with their one-path-per-warp ("wide") form.  Shared by the per-frame and
-// queued kernels, the batched persistent kernel and the adjoint's recompute mode.
+// verdict, and cone tests -- a sampled light's cone per lane, warp cones for point
+// lights and for each batch of rays -- that skip blocks of spheres no segment or ray
+// can reach), register-resident reflection loop, and the bounce queues of the queued
+// render with their one-path-per-warp ("wide") form.  Every skip is proved by an
+// error bound stated beside it, so each result is the brute-force method's, bit for
+// bit.  Shared by the per-frame and queued kernels, the batched persistent kernel and
+// the adjoint's recompute mode.
 #pragma once
 
 #include "rt_bvh.cuh"
@@ -709,11 +713,15 @@ __device__ __forceinline__ uint32_t item_groups(const float4* __restrict__ geo, 
 // cone: the warp's block bits of the cone pre-pass (only the blocks whose bit is set
 // are visited), or null (every block).  items (a full warp, blocks 0..31 only): each
 // lane's own bits `own` instead of the warp's union -- see item_groups.
-template <int R>
+// IT: the item mode compiled in (the queue passes' kernel; in the first pass, whose
+// warps are mostly coherent, its code cost more instruction fetch than it saved).
+template <int R, bool IT>
 __device__ __noinline__ uint32_t occluded_filtered(const float4* __restrict__ geo, int n, unsigned mask, f3 o,
                                                    uint32_t blocked_in, const float* seg, bool exact_only,
                                                    const uint32_t* cone, uint32_t own, bool items) {
-    if (items && !exact_only) return item_groups<R>(geo, o, blocked_in, seg, own);
+    if constexpr (IT) {
+        if (items && !exact_only) return item_groups<R>(geo, o, blocked_in, seg, own);
+    }
     const RayPair o2 = ray_pair(o);
     SegFilt sf[kFiltGroup];
     uint32_t acc[kFiltGroup];
@@ -1003,7 +1011,7 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
 // loop (one copy of the sample code) that writes W and -V to shared memory and the
 // unit vectors for the filter to a local array, and every group tested by
 // occluded_filtered.
-template <bool HITREC>
+template <bool HITREC, bool IT = false>
 __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, const Frame& fr, uint32_t pix, int k,
                                                      f3 p, f3 p_lo, f3 n, f3 po, f3 d, float ks, float e,
                                                      float* __restrict__ hr, size_t hr_k, size_t hr_plane) {
@@ -1103,7 +1111,7 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                         coarse);
         // item mode for the cone's groups where the lanes' own blocks are under a third
         // of the union's steps (a full warp, at most 32 blocks)
-        if (mask == 0xffffffffu && h.ns_pad <= 32 * kPad)
+        if (IT && mask == 0xffffffffu && h.ns_pad <= 32 * kPad)
             items = 3u * __reduce_add_sync(mask, (unsigned)__popc(own)) < 32u * (unsigned)__popc(cw[0]);
     }
     const bool cone_any = cm != 0;
@@ -1179,7 +1187,7 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 cone = cw + kConeWords;
         }
         static_assert(kFiltGroup == 4 && kConeGroup == 4, "one instance: every group has at most 4 segments");
-        blocked = occluded_filtered<kFiltGroup>(sc.geo, h.ns_pad, mask, po, blocked, seg, exact_only, cone, own,
+        blocked = occluded_filtered<kFiltGroup, IT>(sc.geo, h.ns_pad, mask, po, blocked, seg, exact_only, cone, own,
                                                 items && cone == cw);
         // attribute the results to their lights in the same order
 #pragma unroll 1
@@ -1339,7 +1347,7 @@ __device__ __forceinline__ void step_tail(const Frame& fr, int k, float4 m, floa
 // are compiled per path so that each carries only the code it runs.
 constexpr int kShadeAuto = 2;
 
-template <bool HITREC, bool CH, bool ACC, int FM = kShadeAuto>
+template <bool HITREC, bool CH, bool ACC, int FM = kShadeAuto, bool IT = false>
 __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, int id,
                                            float t, f3& o, f3& o_lo, f3& d, float& T, float3& out,
                                            float* __restrict__ hr, size_t hr_k, size_t hr_plane) {
@@ -1353,7 +1361,7 @@ __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& f
     bool filt = false;
     if constexpr (!CH && !ACC) filt = FM == 1 || (FM == kShadeAuto && sc.hdr->ns_pad >= kFilterMinPad);
     if (filt)
-        sh = shade_hit_staged<HITREC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+        sh = shade_hit_staged<HITREC, IT>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
     else
         sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
     step_tail(fr, k, m, m2, sh, n, po, po_lo, o, o_lo, d, T, out);
@@ -1531,7 +1539,7 @@ __device__ __forceinline__ void trace_queued(const StagedScene& sc, const Frame&
     const size_t hr_pix = pix;
 #pragma unroll 1
     while (true) {
-        shade_step<HITREC, false, false, FM>(sc, fr, pix, k, id, t, o, o_lo, d, T, c, hr,
+        shade_step<HITREC, false, false, FM, true>(sc, fr, pix, k, id, t, o, o_lo, d, T, c, hr,
                                          (size_t)k * (2 + h.nl) * hr_plane + hr_pix, hr_plane);
         if (k == fr.D) {
             k = fr.D + 1;
@@ -1682,7 +1690,7 @@ __device__ __forceinline__ HitShade shade_hit_wide(const StagedScene& sc, const 
         seg[4 * kSegStride] = nv.y;
         seg[5 * kSegStride] = nv.z;
         const bool exact_only = !__all_sync(0xffffffffu, ok);
-        const uint32_t blocked = occluded_filtered<1>(sc.geo, h.ns_pad, 0xffffffffu, po, occj ? 1u : 0u, seg,
+        const uint32_t blocked = occluded_filtered<1, false>(sc.geo, h.ns_pad, 0xffffffffu, po, occj ? 1u : 0u, seg,
                                                       exact_only, nullptr, 0u, false);
         const bool vis = valid && !(blocked & 1u);
 #pragma unroll
