@@ -172,40 +172,28 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             const f3 alb = mk3(hg.m.x, hg.m.y, hg.m.z);
             const float ks = hg.m.w, ex = hg.m2.x, rho = hg.m2.y;
             const bool last = (k == fr.D);
-            // forward shading values
-            float A = fr.ka, S = 0.0f;
-            for (int li = 0; li < nl; ++li) {
-                const float4 Lp = h.light_p[li];
-                const f3 lh = normalize_rn(sub(sub(xyz(Lp), hg.p), hg.p_lo));
-                const float ndl = dot(n, lh);
-                if (ndl <= 0.0f) continue;
-                const float v = rec[k * kRecStride + 2 + li];
-                const float sp = light_spec(fr, n, d, lh, ndl, ex);
-                A = fmaf(Lp.w * v, ndl, A);
-                S = fmaf(Lp.w * v * ks, sp, S);
-            }
             const float beta = last ? 1.0f : 1.0f - rho;
-            const f3 R = add(add(scl(alb, beta * A), mk3(S, S, S)), last ? mk3(0.f, 0.f, 0.f) : scl(Rn, rho * A));
             const f3 Rb = scl(g, Tt[k]);
-            // colour terms
-            pg[0] = beta * A * Rb.x;
-            pg[1] = beta * A * Rb.y;
-            pg[2] = beta * A * Rb.z;
+            // the adjoints of A and S do not depend on A and S themselves
             const float Ab = dot(Rb, last ? scl(alb, beta) : add(scl(alb, beta), scl(Rn, rho)));
             const float Sb = Rb.x + Rb.y + Rb.z;
-            pg[4] = last ? 0.0f : dot(Rb, sub(scl(Rn, A), scl(alb, A)));
             f3 pb = mk3(0.f, 0.f, 0.f), nb = mk3(0.f, 0.f, 0.f), db = mk3(0.f, 0.f, 0.f);
-            // lights: A and S
+            // lights, one pass: the forward sums A and S (light order, as the forward
+            // pass forms them) and their adjoints
+            float A = fr.ka, S = 0.0f;
             for (int li = 0; li < nl; ++li) {
                 const float4 Lp = h.light_p[li];
                 float dist;
                 const f3 Lv = sub(sub(xyz(Lp), hg.p), hg.p_lo);
                 const f3 lh = normalize_rn(Lv, &dist);
                 const float ndl = dot(n, lh);
+                if (ndl <= 0.0f) continue;
                 const float v = rec[k * kRecStride + 2 + li];
-                if (ndl <= 0.0f || v == 0.0f) continue;
-                const float I = Lp.w;
                 const float sp = light_spec(fr, n, d, lh, ndl, ex);
+                A = fmaf(Lp.w * v, ndl, A);
+                S = fmaf(Lp.w * v * ks, sp, S);
+                if (v == 0.0f) continue;
+                const float I = Lp.w;
                 lg[li][3] += Ab * v * ndl + Sb * v * ks * sp;
                 pg[3] += Sb * I * v * sp;
                 float ndlb = Ab * I * v;
@@ -243,6 +231,12 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
                 lg[li][2] += Lvb.z;
                 pb = sub(pb, Lvb);
             }
+            const f3 R = add(add(scl(alb, beta * A), mk3(S, S, S)), last ? mk3(0.f, 0.f, 0.f) : scl(Rn, rho * A));
+            // colour terms
+            pg[0] = beta * A * Rb.x;
+            pg[1] = beta * A * Rb.y;
+            pg[2] = beta * A * Rb.z;
+            pg[4] = last ? 0.0f : dot(Rb, sub(scl(Rn, A), scl(alb, A)));
             // the ray that left this hit: origin p + eps n, direction d - 2 (d.n) n
             if (!last) {
                 pb = add(pb, Ob);
