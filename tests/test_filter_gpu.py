@@ -198,3 +198,15 @@ def test_incoherent_warps_with_an_area_light():
     sc.spheres[:, 9] = np.random.default_rng(17).uniform(0.9, 1.0, 160).astype(np.float32)
     p = S._params(sc, width=256, height=160, max_depth=6, shadow_samples=16, out_format=S.OUT_F32, seed=17)
     assert_filter_exact(sc, S.default_camera(0.6), p)
+
+
+def test_ray_cull_far_camera_and_camera_inside_a_sphere():
+    """The closest-hit cull's radius grows with |o| (2^-16 (c_max + |o|)): a camera a
+    million units away with a narrow field of view; and a camera inside a large sphere
+    (every primary ray finds the far root of that sphere)."""
+    sc, cam, p = cluster_scene(seed=19)
+    far = S.f32([0.0, 3e5, -1.3e6, 0.0, -float(np.degrees(np.arctan2(3.0, 13.0))), 0.8])
+    assert_filter_exact(sc, far, p)
+    sph = np.vstack([sc.spheres.astype(np.float64), sphere((0.0, 6.0, -14.0), 3.0, albedo=(0.6, 0.6, 0.6), refl=0.3)])
+    sc2 = S.Scene(spheres=S.f32(sph), plane=sc.plane.copy(), lights=sc.lights.copy(), scale=sc.scale)
+    assert_filter_exact(sc2, cam, p)
