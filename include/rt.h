@@ -41,7 +41,7 @@ typedef enum {
     RT_ERR_INVALID_ARG = 1,   /* a null pointer, size, format or record out of range */
     RT_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed                 */
     RT_ERR_OOM = 3,           /* device or pinned host allocation failed              */
-    RT_ERR_UNSUPPORTED = 4,   /* valid input outside what this build handles          */
+    RT_ERR_UNSUPPORTED = 4,   /* valid input outside what the library handles         */
     RT_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (see rt_device_errors) */
     RT_ERR_EXCEEDS_SCRATCH = 6 /* the work does not fit the fixed scratch of
                                   rt_render_batch_noalloc                             */

@@ -80,7 +80,7 @@ def test_host_validation_rejects_before_any_launch(L):
         d = rt.SceneDesc()
         d.n_spheres, d.spheres = 1, sph.ctypes.data
         assert L.rt_scene_upload(C.byref(d), None, C.byref(h)) == 1
-    # a light inside a sphere: valid input this build does not handle
+    # a light inside a sphere: valid input the library does not handle
     sph = np.array([0, 5, 0, 2, 1, 1, 1, 0.5, 32, 0], np.float32)
     lig = np.array([0, 5.5, 0, 1, 0, 0, 0, 0], np.float32)
     d = rt.SceneDesc()
