@@ -343,6 +343,10 @@ def run_ours(args):
                                            if clocks.get("sm_mhz") else None),
                 "algorithmic_gflop_per_frame": flops_frame / 1e9,
                 "work_basis": f"oracle counters on a {cpu['pixels']}-pixel lattice (stride {cpu['stride']}) x W*H",
+                "note": ("algorithmic work = the brute-force method's sphere tests (17 flop each, up to the first "
+                         "blocker) as the oracle counts them; the kernels prove most of them unnecessary (line "
+                         "filter, cone tests; bit-identical verdicts) and skip them, so frac can exceed 1; the "
+                         "executed load is the FMA pipe's share in the ncu summaries under profiles/"),
             }
         if cpu:
             rec["cpu_baseline"] = {"value": cpu["frames_per_s"], "unit": "frames/s", "cores": cpu["threads"],
