@@ -75,9 +75,9 @@ def _bind(L):
     L.orc_sphere_root.argtypes = [dp, dp, dp, C.c_double, dp]
     L.orc_sphere_root.restype = C.c_int
     L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
-    L.orc_closest.argtypes = [C.POINTER(OrcIn), dp, dp, dp]
+    L.orc_closest.argtypes = [C.POINTER(OrcIn), dp, dp, C.c_int, dp, dp]
     L.orc_closest.restype = C.c_int
-    L.orc_occluded.argtypes = [C.POINTER(OrcIn), dp, dp, C.c_double]
+    L.orc_occluded.argtypes = [C.POINTER(OrcIn), dp, dp, C.c_double, C.c_int, dp]
     L.orc_occluded.restype = C.c_int
     L.orc_light_samples.argtypes = [C.POINTER(OrcIn), C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
     L.orc_light_samples.restype = C.c_int
@@ -233,24 +233,30 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return o
 
 
-def closest(scene, camera, params, o, d):
-    """(id, t) of the closest hit of one ray; id = -1 on a miss."""
+def closest(scene, camera, params, o, d, *, origin: int = -1, margin: bool = False):
+    """(id, t) of the closest hit of one ray; id = -1 on a miss.  origin: the
+    primitive the ray leaves (-1: none).  margin=True: (id, t, the ray's margin)."""
     inp = _In(scene, camera, params)
     o, d = (np.ascontiguousarray(v, np.float64) for v in (o, d))
     t = np.zeros(1, np.float64)
-    i = lib().orc_closest(C.byref(inp.s), _dp(o), _dp(d), _dp(t))
+    m = np.zeros(1, np.float64)
+    i = lib().orc_closest(C.byref(inp.s), _dp(o), _dp(d), int(origin), _dp(t), _dp(m) if margin else None)
     if i < -1:
         raise ValueError("bad input")
-    return i, (float(t[0]) if i >= 0 else None)
+    res = (i, (float(t[0]) if i >= 0 else None))
+    return res + (float(m[0]),) if margin else res
 
 
-def occluded(scene, camera, params, o, d, dist):
+def occluded(scene, camera, params, o, d, dist, *, origin: int = -1, margin: bool = False):
+    """Whether the shadow segment o + t d, 0 < t < dist, is blocked; margin=True:
+    (blocked, the segment's margin)."""
     inp = _In(scene, camera, params)
     o, d = (np.ascontiguousarray(v, np.float64) for v in (o, d))
-    r = lib().orc_occluded(C.byref(inp.s), _dp(o), _dp(d), float(dist))
+    m = np.zeros(1, np.float64)
+    r = lib().orc_occluded(C.byref(inp.s), _dp(o), _dp(d), float(dist), int(origin), _dp(m) if margin else None)
     if r < 0:
         raise ValueError("bad input")
-    return bool(r)
+    return (bool(r), float(m[0])) if margin else bool(r)
 
 
 def light_samples(scene, camera, params, l, x, y, k, p=(0.0, 0.0, 0.0)) -> np.ndarray:

@@ -683,8 +683,10 @@ ORC_API void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_
     philox4x32_10(ctr, key, out);
 }
 /* Closest hit of one ray (id, t; id = -1 on a miss) and the any-hit test of one
- * shadow segment, for the brute-force pin tests. */
-ORC_API int orc_closest(const orc_in *in, const double *o, const double *d, double *t)
+ * shadow segment, for the brute-force and margin pin tests.  `origin` is the
+ * primitive the ray leaves (-1: none); margin (nullable) receives the ray's margin. */
+ORC_API int orc_closest(const orc_in *in, const double *o, const double *d, int origin, double *t,
+                        double *margin)
 {
     Ctx cx;
     int st = build_ctx(in, &cx);
@@ -692,13 +694,17 @@ ORC_API int orc_closest(const orc_in *in, const double *o, const double *d, doub
     Path P;
     memset(&P, 0, sizeof(P));
     P.cx = &cx;
-    P.origin = -1;
+    P.origin = origin;
+    P.want_margin = margin != NULL;
+    P.margin = INFINITY;
     int id = closest_hit(&P, V(o[0], o[1], o[2]), V(d[0], d[1], d[2]), t);
+    if (margin) *margin = P.margin;
     free(cx.prim);
     free(cx.light);
     return id;
 }
-ORC_API int orc_occluded(const orc_in *in, const double *o, const double *d, double dist)
+ORC_API int orc_occluded(const orc_in *in, const double *o, const double *d, double dist, int origin,
+                         double *margin)
 {
     Ctx cx;
     int st = build_ctx(in, &cx);
@@ -706,8 +712,11 @@ ORC_API int orc_occluded(const orc_in *in, const double *o, const double *d, dou
     Path P;
     memset(&P, 0, sizeof(P));
     P.cx = &cx;
-    P.origin = -1;
+    P.origin = origin;
+    P.want_margin = margin != NULL;
+    P.margin = INFINITY;
     int hit = occluded(&P, V(o[0], o[1], o[2]), V(d[0], d[1], d[2]), dist);
+    if (margin) *margin = P.margin;
     free(cx.prim);
     free(cx.light);
     return hit;

@@ -568,6 +568,117 @@ def pin_margin_grazing(orc):
         assert abs(m - abs(h - 1.0)) < 1e-9, (x, m, h)
 
 
+H_GRAZE = 2.0 ** -7        # a small distance exact in FP32
+
+
+def _close(a, b, tol=1e-12):
+    return abs(a - b) <= tol * max(1.0, abs(b))
+
+
+def pin_margin_closest_terms(orc):
+    """Margins of one closest-hit ray (the distances below which FP32 could decide
+    the hit differently: Section 3.4's closest-hit decision), in closed form along
+    the +z axis from the origin:
+      gap to the second primitive: spheres at depth 9 and 9 + h -> h, in either
+      index order; the plane at depth 9 + h behind a sphere hit at 9 -> h;
+      plane horizon: a ray at slope s to the plane y = 0 -> s * scene scale, hit or
+      miss (the scene scale being the sphere box's half-extent, 5 length units
+      per unit of scale); a root near the origin: the plane h below -> h, a sphere surface h
+      behind -> h, neither counted when the ray leaves that primitive;
+      a silhouette grazed at distance h in front of the hit -> h, but not behind
+      the hit and not behind the origin."""
+    h = H_GRAZE
+    o, z = np.zeros(3), np.array([0.0, 0.0, 1.0])
+    A, B = sphere((0, 0, 10), 1.0), sphere((0, 0, 10 + h), 1.0)
+    for sph in ([A, B], [B, A]):
+        sc, cam, p = mk(spheres=sph)
+        i, t, m = orc.closest(sc, cam, p, o, z, margin=True)
+        assert sph[i] is A and t == 9.0 and _close(m, h), (i, t, m)
+    sc, cam, p = mk(spheres=[A], plane=plane_rec(n=(0, 0, 1), d=-(9 + h)))
+    i, t, m = orc.closest(sc, cam, p, o, z, margin=True)
+    assert i == 0 and _close(m, h), (i, m)
+    s = 0.01
+    for scale in (1.0, 2.0):
+        sc, cam, p = mk(plane=plane_rec(), scale=scale)
+        for sign, want_id in ((-1.0, 0), (1.0, -1)):
+            d = np.array([math.sqrt(1 - s * s), sign * s, 0.0])
+            i, t, m = orc.closest(sc, cam, p, np.array([0.0, 1.0, 0.0]), d, margin=True)
+            assert i == want_id and _close(m, s * sc.scene_scale), (scale, sign, i, m)
+    sc, cam, p = mk(plane=plane_rec(), scale=1.0)
+    assert sc.scene_scale > 1.0
+    down = np.array([0.0, -1.0, 0.0])
+    i, t, m = orc.closest(sc, cam, p, np.array([0.0, h, 0.0]), down, margin=True)
+    assert i == 0 and _close(t, h) and _close(m, h), (i, t, m)
+    i, t, m = orc.closest(sc, cam, p, np.array([0.0, h, 0.0]), down, origin=0, margin=True)
+    assert i == 0 and _close(m, sc.scene_scale), m
+    sc, cam, p = mk(spheres=[sphere((0, 0, -1 - h), 1.0)])
+    i, t, m = orc.closest(sc, cam, p, o, z, margin=True)
+    assert i == -1 and _close(m, h), (i, m)
+    i, t, m = orc.closest(sc, cam, p, o, z, origin=0, margin=True)
+    assert i == -1 and math.isinf(m), m
+    for cz, want in ((5.0, h), (20.0, 9.0)):
+        sc, cam, p = mk(spheres=[A, sphere((1 + h, 0, cz), 1.0)])
+        i, t, m = orc.closest(sc, cam, p, o, z, margin=True)
+        assert i == 0 and _close(m, want), (cz, i, m)
+    sc, cam, p = mk(spheres=[sphere((1 + h, 0, -5), 1.0)])
+    i, t, m = orc.closest(sc, cam, p, o, z, margin=True)
+    assert i == -1 and math.isinf(m), m
+
+
+def pin_margin_shadow_terms(orc):
+    """Margins of one shadow segment o + t z, 0 < t < dist (Section 3.6's
+    cast-shadow decision), in closed form: a sphere spanning depths 9..11 and
+    the light h before its near surface, h inside it, or h beyond its far
+    surface -> h; a sphere surface h ahead of the origin -> h (not counted when
+    the segment leaves that sphere: then the silhouette term, r = 1); a
+    silhouette grazed at h between origin and light -> h, but not beyond the
+    light or behind the origin; the plane y = 0 crossed h before or after the
+    light -> h; the plane h behind the origin -> h, not counted when the
+    segment leaves the plane."""
+    h = H_GRAZE
+    o, z = np.zeros(3), np.array([0.0, 0.0, 1.0])
+    sc, cam, p = mk(spheres=[sphere((0, 0, 10), 1.0)])
+    for dist, blocked in ((9 - h, False), (9 + h, True), (11 + h, True)):
+        b, m = orc.occluded(sc, cam, p, o, z, dist, margin=True)
+        assert b == blocked and _close(m, h), (dist, b, m)
+    sc, cam, p = mk(spheres=[sphere((0, 0, 1 + h), 1.0)])
+    b, m = orc.occluded(sc, cam, p, o, z, 100.0, margin=True)
+    assert b and _close(m, h), (b, m)
+    b, m = orc.occluded(sc, cam, p, o, z, 100.0, origin=0, margin=True)
+    assert b and _close(m, 1.0), (b, m)
+    for cz, want in ((5.0, h), (15.0, math.inf), (-5.0, math.inf)):
+        sc, cam, p = mk(spheres=[sphere((1 + h, 0, cz), 1.0)])
+        b, m = orc.occluded(sc, cam, p, o, z, 10.0, margin=True)
+        assert not b and (_close(m, want) if want < math.inf else math.isinf(m)), (cz, b, m)
+    sc, cam, p = mk(plane=plane_rec())
+    down = np.array([0.0, -1.0, 0.0])
+    for dist, blocked in ((1 - h, False), (1 + h, True)):
+        b, m = orc.occluded(sc, cam, p, np.array([0.0, 1.0, 0.0]), down, dist, margin=True)
+        assert b == blocked and _close(m, h), (dist, b, m)
+    up = np.array([0.0, 1.0, 0.0])
+    b, m = orc.occluded(sc, cam, p, np.array([0.0, h, 0.0]), up, 5.0, margin=True)
+    assert not b and _close(m, h), (b, m)
+    b, m = orc.occluded(sc, cam, p, np.array([0.0, h, 0.0]), up, 5.0, origin=0, margin=True)
+    assert not b and _close(m, 5.0 + h), (b, m)
+
+
+def pin_margin_light_gate(orc):
+    """The light gate n.l > 0 (Section 3.5 with the shadow rays of Section 3.6)
+    decides whether a light contributes at all; its margin is |n.l| x scene scale.
+    A camera looking straight down at the plane y = 0 from height 10 sees the
+    origin in its centre pixel; a light at (10, +-y_l, 0) grazes it, n.l =
+    y_l / |L|, and every other term of that pixel's path is larger."""
+    yl = 0.0625
+    for scale in (1.0, 2.0):
+        for sgn in (1.0, -1.0):
+            Lp = (10.0, sgn * yl, 0.0)
+            sc, cam, p = mk(plane=plane_rec(), lights=[light(Lp)], camera=(0, 10, 0, 0, -90, 60), W=4, H=4,
+                            scale=scale)
+            m = orc.trace(sc, cam, p, np.array([[2, 2]], np.int32), margin=True, threads=1)["margin"][0]
+            want = yl / math.hypot(10.0, yl) * sc.scene_scale
+            assert _close(m, want, 1e-9), (scale, sgn, m, want)
+
+
 def pin_rgba8(orc):
     """toInt reading: clamp, x 255, round half up, alpha 255, 0xAABBGGRR."""
     rgb = np.array([[0.5, 0.25, 1.5], [-1.0, 0.0, 1.0], [0.2, 0.6, 0.999]])

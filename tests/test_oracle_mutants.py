@@ -15,7 +15,8 @@ ORDER = ["pin_ndc_worked_example", "pin_ndc_shorter_side_spans_unit_square",
          "pin_camera_distance", "pin_primary_ray", "pin_ray_sphere_closed_forms",
          "pin_ties_lowest_index", "pin_phong_closed_forms", "pin_single_sphere_lit_side", "pin_blinn_closed_form",
          "pin_plane_horizon", "pin_occlusion_invariant", "pin_philox_kat", "pin_rgba8",
-         "pin_margin_grazing", "pin_counters", "pin_area_samples_stratified", "pin_vogel_sunflower",
+         "pin_margin_grazing", "pin_margin_closest_terms", "pin_margin_shadow_terms", "pin_margin_light_gate",
+         "pin_counters", "pin_area_samples_stratified", "pin_vogel_sunflower",
          "pin_reflection_mixing_closed_form", "pin_coupled_reflectivity",
          "pin_depth_reductions", "pin_area_light", "pin_mirror_symmetry",
          "pin_sky_invariants", "pin_sky_on_misses", "pin_verlet_free_fall", "pin_verlet_ground_contact",
@@ -81,6 +82,32 @@ MUTANTS = {
     "verlet_no_pushout": ("xn = sub(xn, scl(nn, sd));", ""),
     "verlet_no_rest_contact": ("-vn <= 2.0 * gdt2 ? vn : (1.0 + e) * vn", "(1.0 + e) * vn"),
     "verlet_prev_not_reset": ("xq = sub(xn, v);", "xq = x;"),
+    # margins (the exemption from the colour tolerance is decided by them)
+    "margin_gap_dropped": ("if (best >= 0 && t2 < INFINITY) m = fmin(m, t2 - tb);", ""),
+    "margin_plane_gap_dropped": ("if (best != cx->ns && tp > 0.0) t2 = fmin(t2, tp);", ""),
+    "margin_horizon_dropped": ("if (best == cx->ns || best < 0) m = fmin(m, fabs(den) * cx->S);", ""),
+    "margin_horizon_unscaled": ("m = fmin(m, fabs(den) * cx->S);", "m = fmin(m, fabs(den));"),
+    "margin_horizon_only_on_plane_hits": ("if (best == cx->ns || best < 0) m", "if (best == cx->ns) m"),
+    "margin_closest_plane_root_dropped": ("if (P->origin != cx->ns) m = fmin(m, fabs(tp));\n            if (best",
+                                          "if (best"),
+    "margin_closest_roots_dropped": ("m = fmin(m, fabs(tca - sq));\n            m = fmin(m, fabs(tca + sq));", ""),
+    "margin_closest_origin_not_skipped": ("if (disc >= 0.0 && i != P->origin) {", "if (disc >= 0.0) {"),
+    "margin_silhouette_behind_hit": ("(best < 0 || tca - s->r < tb)", "(1)"),
+    "margin_silhouette_behind_origin": ("if (tca + s->r > 0.0 && ", "if ("),
+    "margin_shadow_endpoints_dropped": ("m = fmin(m, fabs(r1 - dist));\n                m = fmin(m, fabs(r2 - dist));",
+                                        ""),
+    "margin_shadow_far_endpoint_dropped": ("m = fmin(m, fabs(r2 - dist));", ""),
+    "margin_shadow_origin_roots_dropped": ("if (i != P->origin) m = fmin(m, fmin(fabs(r1), fabs(r2)));", ""),
+    "margin_shadow_origin_not_skipped": ("if (i != P->origin) m = fmin(m, fmin(fabs(r1), fabs(r2)));",
+                                         "m = fmin(m, fmin(fabs(r1), fabs(r2)));"),
+    "margin_shadow_silhouette_dropped": ("if (tca >= 0.0 && tca <= dist) m = fmin(m, fabs(ld - s->r));", ""),
+    "margin_shadow_silhouette_beyond_light": ("if (tca >= 0.0 && tca <= dist)", "if (tca >= 0.0)"),
+    "margin_shadow_plane_endpoint_dropped": ("m = fmin(m, fabs(tp - dist));", ""),
+    "margin_shadow_plane_origin_dropped": (
+        "m = fmin(m, fabs(tp - dist));\n                if (P->origin != cx->ns) m = fmin(m, fabs(tp));",
+        "m = fmin(m, fabs(tp - dist));"),
+    "margin_light_gate_dropped": ("if (P->want_margin) P->margin = fmin(P->margin, fabs(ndl) * cx->S);", ""),
+    "margin_light_gate_unscaled": ("fabs(ndl) * cx->S", "fabs(ndl)"),
 }
 
 
