@@ -79,6 +79,8 @@ def _bind(L):
     L.orc_closest.restype = C.c_int
     L.orc_occluded.argtypes = [C.POINTER(OrcIn), dp, dp, C.c_double, C.c_int, dp]
     L.orc_occluded.restype = C.c_int
+    L.orc_trace_path.argtypes = [C.POINTER(OrcIn), C.c_int, C.c_int, dp]
+    L.orc_trace_path.restype = C.c_int
     L.orc_light_samples.argtypes = [C.POINTER(OrcIn), C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
     L.orc_light_samples.restype = C.c_int
     L.orc_sky.argtypes = [C.POINTER(C.c_float), C.c_int, C.c_int, dp, dp]
@@ -257,6 +259,18 @@ def occluded(scene, camera, params, o, d, dist, *, origin: int = -1, margin: boo
     if r < 0:
         raise ValueError("bad input")
     return (bool(r), float(m[0])) if margin else bool(r)
+
+
+def trace_path(scene, camera, params, x: int, y: int) -> np.ndarray:
+    """The ray path of pixel (x, y): [n, 14] rows (id, t, origin 3, direction 3,
+    hit point 3, normal 3) per bounce, the last row a miss (id -1) if the path
+    leaves the scene before the bounce limit."""
+    inp = _In(scene, camera, params)
+    out = np.zeros((int(params.max_depth) + 1, 14), np.float64)
+    n = lib().orc_trace_path(C.byref(inp.s), int(x), int(y), _dp(out))
+    if n < 0:
+        raise ValueError("bad input")
+    return out[:n].copy()
 
 
 def light_samples(scene, camera, params, l, x, y, k, p=(0.0, 0.0, 0.0)) -> np.ndarray:

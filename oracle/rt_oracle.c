@@ -421,12 +421,16 @@ static void shade_terms(Path *P, int k, v3 p, v3 n, v3 d, const Prim *m, double 
     *S = s;
 }
 
-/* Geometry at a hit: point, face-forwarded normal (sphere (p - c)/r, plane n;
- * reading: flipped to face the incoming ray). */
+/* Geometry at a hit: point and unit normal, face-forwarded (reading: flipped to
+ * face the incoming ray).  Sphere: the unit vector from the centre through the
+ * hit point, normalize(p - c) -- equal to (p - c)/r on the surface; evaluated as
+ * a normalisation so that the rounding of the root cannot make |n| differ from 1
+ * (the reflection below keeps |d| = 1 only for a unit n, and the root formula
+ * assumes a unit d).  Plane: its unit normal. */
 static void hit_geometry(const Ctx *cx, int id, v3 o, v3 d, double t, v3 *p, v3 *n)
 {
     *p = add(o, scl(d, t));
-    if (id < cx->ns) *n = scl(sub(*p, cx->prim[id].g), 1.0 / cx->prim[id].r);
+    if (id < cx->ns) *n = nrm(sub(*p, cx->prim[id].g));
     else *n = cx->prim[id].g;
     if (dot(*n, d) > 0.0) *n = scl(*n, -1.0);
 }
@@ -720,6 +724,41 @@ ORC_API int orc_occluded(const orc_in *in, const double *o, const double *d, dou
     free(cx.prim);
     free(cx.light);
     return hit;
+}
+
+/* The path of pixel (x, y) for the pin tests: per bounce k = 0..D one record of 14
+ * doubles (id, t, origin xyz, direction xyz, hit point xyz, normal xyz; id = -1 on
+ * a miss, which ends the path), following the forward form's ray sequence
+ * (Section 3.7.1: reflected direction d - 2 (d.n) n, origin p + eps n).  Returns
+ * the number of records written. */
+ORC_API int orc_trace_path(const orc_in *in, int x, int y, double *rec)
+{
+    Ctx cx;
+    int st = build_ctx(in, &cx);
+    if (st) return -100 + st;
+    Path P;
+    memset(&P, 0, sizeof(P));
+    P.cx = &cx;
+    P.origin = -1;
+    v3 o, d;
+    primary_ray(&cx, x, y, 0.0, 0.0, &o, &d);
+    int n_rec = 0;
+    for (int k = 0; k <= cx.D; ++k) {
+        double t;
+        const int id = closest_hit(&P, o, d, &t);
+        double *r = rec + 14 * n_rec++;
+        v3 p = V(0.0, 0.0, 0.0), nn = V(0.0, 0.0, 0.0);
+        if (id >= 0) hit_geometry(&cx, id, o, d, t, &p, &nn);
+        const double vals[14] = {id, id >= 0 ? t : 0.0, o.x, o.y, o.z, d.x, d.y, d.z, p.x, p.y, p.z, nn.x, nn.y, nn.z};
+        memcpy(r, vals, sizeof(vals));
+        if (id < 0) break;
+        P.origin = id;
+        d = sub(d, scl(nn, 2.0 * dot(d, nn)));
+        o = add(p, scl(nn, cx.eps));
+    }
+    free(cx.prim);
+    free(cx.light);
+    return n_rec;
 }
 
 /* Sample points of sampled light l seen from point p at pixel (x, y), bounce k

@@ -679,6 +679,51 @@ def pin_margin_light_gate(orc):
             assert _close(m, want, 1e-9), (scale, sgn, m, want)
 
 
+# pixels of the 3840x2160 seeded workload whose paths run six to nine bounces
+# between spheres (found by scanning the frame): chains where rounding in the
+# hit geometry is amplified most from bounce to bounce
+DEEP_4K_PIXELS = [(1849, 695), (2767, 705), (1535, 707), (1558, 707), (2044, 711), (2642, 712), (2643, 712),
+                  (1549, 714), (2395, 717), (2412, 717), (2056, 725), (1660, 730)]
+
+
+def pin_path_geometry_invariants(orc):
+    """Along every ray path (Sections 3.4, 3.5, 3.7.1): each hit point lies on its
+    primitive (|p - c| = r, or the plane equation), each normal and direction has
+    unit length, the normal faces the incoming ray, and the next ray leaves from
+    p + eps n along the mirror direction d - 2 (d.n) n.  Checked on deep
+    reflection chains of the 4K workload and on a lattice of its pixels."""
+    w = S.area_4k()
+    sph = np.asarray(w.scene.spheres, np.float64).reshape(-1, 10)
+    pl = np.asarray(w.scene.plane, np.float64)
+    eps = float(w.params.eps)
+    pixels = DEEP_4K_PIXELS + [(x, y) for y in range(0, 2160, 157) for x in range(0, 3840, 263)]
+    deep = 0
+    for x, y in pixels:
+        P = orc.trace_path(w.scene, w.camera, w.params, x, y)
+        o0, d0 = orc.primary_ray(w.scene, w.camera, w.params, x, y)
+        assert np.array_equal(P[0, 2:5], o0) and np.array_equal(P[0, 5:8], d0)
+        for k, row in enumerate(P):
+            i = int(row[0])
+            o, d, p, n = row[2:5], row[5:8], row[8:11], row[11:14]
+            assert abs(np.linalg.norm(d) - 1.0) < 1e-12, (x, y, k, np.linalg.norm(d))
+            if i < 0:
+                assert k == len(P) - 1
+                continue
+            assert np.allclose(p, o + row[1] * d, rtol=0, atol=1e-12 * (1 + np.abs(p).max()))
+            if i < len(sph):
+                assert abs(np.linalg.norm(p - sph[i, :3]) / sph[i, 3] - 1.0) < 1e-9, (x, y, k, i)
+            else:
+                assert abs(np.dot(pl[:3], p) + pl[3]) < 1e-9 * (1 + np.abs(p).max()), (x, y, k)
+            assert abs(np.linalg.norm(n) - 1.0) < 1e-12, (x, y, k, np.linalg.norm(n))
+            assert np.dot(n, d) <= 0.0, (x, y, k)
+            if k + 1 < len(P):
+                nxt = P[k + 1]
+                assert np.allclose(nxt[5:8], d - 2 * np.dot(d, n) * n, rtol=0, atol=1e-14)
+                assert np.allclose(nxt[2:5], p + eps * n, rtol=0, atol=1e-13 * (1 + np.abs(p).max()))
+        deep += len(P) >= 7
+    assert deep >= 8
+
+
 def pin_rgba8(orc):
     """toInt reading: clamp, x 255, round half up, alpha 255, 0xAABBGGRR."""
     rgb = np.array([[0.5, 0.25, 1.5], [-1.0, 0.0, 1.0], [0.2, 0.6, 0.999]])

@@ -20,7 +20,7 @@ ORDER = ["pin_ndc_worked_example", "pin_ndc_shorter_side_spans_unit_square",
          "pin_reflection_mixing_closed_form", "pin_coupled_reflectivity",
          "pin_depth_reductions", "pin_area_light", "pin_mirror_symmetry",
          "pin_sky_invariants", "pin_sky_on_misses", "pin_verlet_free_fall", "pin_verlet_ground_contact",
-         "pin_recursion_equals_loop", "pin_occlusion_brute_force",
+         "pin_recursion_equals_loop", "pin_path_geometry_invariants", "pin_occlusion_brute_force",
          "pin_closest_hit_brute_force"]
 
 MUTANTS = {
@@ -82,6 +82,8 @@ MUTANTS = {
     "verlet_no_pushout": ("xn = sub(xn, scl(nn, sd));", ""),
     "verlet_no_rest_contact": ("-vn <= 2.0 * gdt2 ? vn : (1.0 + e) * vn", "(1.0 + e) * vn"),
     "verlet_prev_not_reset": ("xq = sub(xn, v);", "xq = x;"),
+    "sphere_normal_over_radius": ("*n = nrm(sub(*p, cx->prim[id].g));",
+                                  "*n = scl(sub(*p, cx->prim[id].g), 1.0 / cx->prim[id].r);"),
     # margins (the exemption from the colour tolerance is decided by them)
     "margin_gap_dropped": ("if (best >= 0 && t2 < INFINITY) m = fmin(m, t2 - tb);", ""),
     "margin_plane_gap_dropped": ("if (best != cx->ns && tp > 0.0) t2 = fmin(t2, tp);", ""),
