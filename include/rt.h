@@ -316,8 +316,11 @@ rt_status rt_batch_free(rt_batch *batch);
  *     rt_batch_workspace_bytes) at most RT_NOALLOC_SCRATCH_BYTES: otherwise
  *     RT_ERR_EXCEEDS_SCRATCH and nothing is enqueued.
  *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress, with that device current).
+ *   - It must not be captured into a CUDA graph: a captured copy would read the
+ *     shared static host image when the graph replays, after later calls have
+ *     rewritten it.  A call on a stream that is capturing returns
+ *     RT_ERR_UNSUPPORTED and enqueues nothing (checked before any set-up).
  *   - Every call reuses the same array (the copy rewrites it, including the work
  *     counter, which it resets to zero): calls whose work overlaps on the GPU,
  *     on any stream, race.  Order them (same stream or events). */

@@ -1407,11 +1407,18 @@ rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera
 extern "C" rt_status rt_render_batch_noalloc(int32_t n, const rt_scene* const* scenes, const rt_camera* cams,
                                              const rt_render_params* params, void* const* outs_dev,
                                              const size_t* pitches, const rt_launch_config* cfg, void* stream) {
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    // A captured call would record a copy from the shared static host image, which a
+    // later call overwrites before the graph replays: refuse capture, before any set-up.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st_, &cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (cap != cudaStreamCaptureStatusNone) return RT_ERR_UNSUPPORTED;
     Launch L;
     rt_status st = resolve_launch(cfg, &L);
     if (st != RT_OK) return st;
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 0 || dev >= kMaxDevices) return RT_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> guard(g_noalloc_mu);
@@ -1431,7 +1438,6 @@ extern "C" rt_status rt_render_batch_noalloc(int32_t n, const rt_scene* const* s
     if ((st = batch_smem(chunked, smem)) != RT_OK) return st;
     int grid = 0;
     if ((st = batch_grid(L, smem, chunked, &grid)) != RT_OK) return st;
-    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     // pageable source: staged by the runtime before the call returns, so the static
     // host image is free for the next call
     e = cudaMemcpyAsync(g_noalloc_dev_ptr[dev], g_noalloc_host, bytes, cudaMemcpyHostToDevice, st_);
