@@ -189,6 +189,85 @@ def recorded_traffic(workload_name: str, kernel: str = "rt_fwd_kernel"):
     return None
 
 
+# Executed FP32 work and hardware load of the forward kernels of one frame, from an ncu
+# capture of the same sources (profiles/executed.txt); FP32 flops = fadd + fmul + 2 ffma
+# + 2 fadd2 + 2 fmul2 + 4 ffma2 thread instructions (a packed f32x2 instruction does two
+# operations per thread).
+EXEC_FIELDS = ("fp32_flop", "fma_pipe_pct", "issue_active_pct", "no_instruction_per_issue", "lanes_per_inst",
+               "dram_read_bytes", "dram_write_bytes", "ncu_ms")
+
+
+def recorded_executed(workload_name: str, kernel: str):
+    path = os.path.join(ROOT, "profiles", "executed.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for ln in open(path):
+        f = ln.split("#", 1)[0].split()
+        if len(f) == 3 + len(EXEC_FIELDS) and f[0] == kernel and f[1] == want \
+                and f[2] == workload_name:
+            return dict(zip(EXEC_FIELDS, map(float, f[3:])))
+    return None
+
+
+def ingest_ncu(csv_paths, kernel: str, workload_name: str) -> str:
+    """One line of profiles/executed.txt from ncu --csv logs of one frame's launches
+    (the metrics of EXEC_METRICS): sums over the launches, pipe and issue shares
+    weighted by launch duration."""
+    import csv
+    rows = {}
+    for p in csv_paths:
+        with open(p) as f:
+            lines = [ln for ln in f if ln.startswith('"')]
+        for r in csv.DictReader(lines):
+            key = (p, r["ID"])
+            v = float(r["Metric Value"].replace(",", "") or 0)
+            v *= UNIT_SCALE.get(r.get("Metric Unit", "").strip(), 1.0)
+            rows.setdefault(key, {})[r["Metric Name"]] = v
+    tot = dict.fromkeys(EXEC_FIELDS, 0.0)
+    wsum = 0.0
+    for m in rows.values():
+        ms = m.get("gpu__time_duration.sum", 0.0) / 1e6
+        th = lambda op: m.get(f"sm__sass_thread_inst_executed_op_{op}_pred_on.sum", 0.0)  # noqa: E731
+        tot["fp32_flop"] += th("fadd") + th("fmul") + 2 * th("ffma") + 2 * th("fadd2") + 2 * th("fmul2") \
+            + 4 * th("ffma2")
+        tot["fma_pipe_pct"] += ms * m.get("sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active", 0.0)
+        tot["issue_active_pct"] += ms * m.get("smsp__issue_active.avg.pct_of_peak_sustained_active", 0.0)
+        tot["no_instruction_per_issue"] += ms * m.get(
+            "smsp__average_warps_issue_stalled_no_instruction_per_issue_active.ratio", 0.0)
+        tot["lanes_per_inst"] += m.get("smsp__thread_inst_executed.sum", 0.0)
+        tot["dram_read_bytes"] += m.get("dram__bytes_read.sum", 0.0)
+        tot["dram_write_bytes"] += m.get("dram__bytes_write.sum", 0.0)
+        tot["ncu_ms"] += ms
+        wsum += m.get("smsp__inst_executed.sum", 0.0)
+    for k in ("fma_pipe_pct", "issue_active_pct", "no_instruction_per_issue"):
+        tot[k] /= max(tot["ncu_ms"], 1e-12)
+    tot["lanes_per_inst"] /= max(wsum, 1.0)
+    vals = " ".join(f"{tot[k]:.6g}" for k in EXEC_FIELDS)
+    return f"{kernel} {kernel_source_hash()} {workload_name} {vals}  # {len(rows)} launches"
+
+
+# ncu units to base units (bytes, nanoseconds); captures use --print-units base
+UNIT_SCALE = {"Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "usecond": 1e3, "msecond": 1e6, "second": 1e9}
+
+EXEC_METRICS = ",".join([
+    "gpu__time_duration.sum", "dram__bytes_read.sum", "dram__bytes_write.sum",
+    *[f"sm__sass_thread_inst_executed_op_{op}_pred_on.sum" for op in ("fadd", "fmul", "ffma", "fadd2", "fmul2", "ffma2")],
+    "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active",
+    "smsp__issue_active.avg.pct_of_peak_sustained_active",
+    "smsp__average_warps_issue_stalled_no_instruction_per_issue_active.ratio",
+    "smsp__thread_inst_executed.sum", "smsp__inst_executed.sum"])
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6400.0, "of fallback (6.4 TB/s)"
+
+
 def workload_config(w: S.Workload, world: int) -> dict:
     """The `config` object of both arms' JSON lines: what the workload is."""
     return {"workload": w.name, "width": w.params.width, "height": w.params.height, "spheres": w.scene.n_spheres,
@@ -332,10 +411,13 @@ def run_ours(args):
             achieved = flops_frame / (ms_step / 1e3) / 1e12
             peak_max = sm_count * 128 * 2 * 2032e6 / 1e12
             rec["mrays_per_s"] = rays_frame * fps / 1e6
+            kset = "rt_render_ws" if wsbuf is not None else "rt_fwd_kernel"
             rec["roofline"] = {
                 "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
                 "frac": achieved / peak_max,
-                "traffic": recorded_traffic(w.name, "rt_render_ws" if wsbuf is not None else "rt_fwd_kernel"),
+                "frac_basis": "algorithmic (the brute-force method's FP32 work per frame / frame time / peak)",
+                "algorithmic_frac": achieved / peak_max,
+                "traffic": recorded_traffic(w.name, kset),
                 "kernel": ("rt_fwd_p0_kernel + rt_fwd_queue_kernel x D (rt_render_ws: one frame = 1 + D launches, "
                            "timed together)" if wsbuf is not None else "rt_fwd_kernel"),
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)",
@@ -345,9 +427,29 @@ def run_ours(args):
                 "work_basis": f"oracle counters on a {cpu['pixels']}-pixel lattice (stride {cpu['stride']}) x W*H",
                 "note": ("algorithmic work = the brute-force method's sphere tests (17 flop each, up to the first "
                          "blocker) as the oracle counts them; the kernels prove most of them unnecessary (line "
-                         "filter, cone tests; bit-identical verdicts) and skip them, so frac can exceed 1; the "
-                         "executed load is the FMA pipe's share in the ncu summaries under profiles/"),
+                         "filter, cone tests; bit-identical verdicts) and skip them, so frac can exceed 1; "
+                         "executed_frac is the FP32 work the kernels do execute (ncu instruction counts of the "
+                         "same sources) per frame time, against the same peak"),
             }
+            ex = recorded_executed(w.name, kset)
+            fb_bytes = out.numel() * out.element_size()
+            hbm = measured_hbm_gbs()
+            rec["roofline"].update({
+                "executed_frac": (ex["fp32_flop"] / (ms_step / 1e3) / 1e12 / peak_max) if ex else None,
+                "executed_tflops": (ex["fp32_flop"] / (ms_step / 1e3) / 1e12) if ex else None,
+                "executed_gflop_per_frame": ex["fp32_flop"] / 1e9 if ex else None,
+                "fma_pipe_busy_pct": ex["fma_pipe_pct"] if ex else None,
+                "issue_active_pct": ex["issue_active_pct"] if ex else None,
+                "no_instruction_stalls_per_issue": ex["no_instruction_per_issue"] if ex else None,
+                "warp_exec_eff": ex["lanes_per_inst"] / 32.0 if ex else None,
+                "framebuffer_write_gbs": fb_bytes / (ms_step / 1e3) / 1e9,
+                "framebuffer_write_frac_of_hbm": fb_bytes / (ms_step / 1e3) / 1e9 / hbm[0],
+                "hbm_peak_gbs": hbm[0], "hbm_peak_basis": hbm[1],
+                "executed_basis": ("ncu instruction counts of one frame's launches on the current kernel sources "
+                                   "(profiles/executed.txt; FP32 flops = fadd + fmul + 2 ffma + 2 fadd2 + 2 fmul2 + "
+                                   "4 ffma2 thread instructions), per CUDA-event frame time"
+                                   if ex else "no ncu record for the current kernel sources"),
+            })
         if cpu:
             rec["cpu_baseline"] = {"value": cpu["frames_per_s"], "unit": "frames/s", "cores": cpu["threads"],
                                    "kind": "oracle",
@@ -616,12 +718,16 @@ def profile_render(args):
     launch = {"accel": 1} if args.accel else None
     if args.accel:
         ds.build_bvh()
-    wsbuf = rt.alloc_workspace(ds, w.params) if args.queued else None
+    if args.tuned:
+        from paper_2305_07450_b300 import autotune
+        launch = autotune.tune_render(ds, w.scene, w.camera, w.params)
+    wsbuf = rt.alloc_workspace(ds, w.params) if (args.queued or (launch or {}).get("queued")) else None
     for _ in range(args.warmup + args.steps):
         rt.render(ds, w.camera, w.params, out=out, pitch=pitch, launch=launch, workspace=wsbuf)
     torch.cuda.synchronize()
     assert rt.device_errors() == 0
-    print(json.dumps({"profile_render": w.name, "accel": bool(args.accel), "queued": bool(args.queued),
+    print(json.dumps({"profile_render": w.name, "accel": bool(args.accel), "queued": wsbuf is not None,
+                      "launch": launch,
                       "frames": args.warmup + args.steps}))
 
 
@@ -653,11 +759,19 @@ def main(argv=None):
                     help="only render the workload (warmup + steps launches, default launch), for ncu")
     ap.add_argument("--accel", action="store_true", help="with --profile-render: through the sphere hierarchy")
     ap.add_argument("--queued", action="store_true", help="with --profile-render: rt_render_ws (queued passes)")
+    ap.add_argument("--tuned", action="store_true",
+                    help="with --profile-render: the autotuned launch the bench times (queued if it chose so)")
+    ap.add_argument("--ingest-ncu", nargs="+", metavar="CSV",
+                    help="print the profiles/executed.txt line of ncu --csv logs (EXEC_METRICS) of one frame")
+    ap.add_argument("--kernel-set", default="rt_render_ws", help="with --ingest-ncu: the record's kernel column")
     ap.add_argument("--profile-batch", action="store_true",
                     help="only launch the 64-scene batch graph --warmup + --steps times (a profiling target)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.ingest_ncu:
+        print(ingest_ncu(args.ingest_ncu, args.kernel_set, workload(args.workload).name))
+        return None
     if args.profile_batch:
         return profile_batch(args)
     if args.profile_render:

@@ -10,10 +10,20 @@ pixel that does not is accepted only when
     chains off curved surfaces amplify direction errors by about 2t/r per
     bounce, so an FP32 renderer can only match the FP64 definition to within
     this sensitivity.
+Every comparison reports how many pixels pass plainly and how many rely on each
+exemption, and the tests bound the exempt share (at most 1e-4 of the pixels, the
+share the RGBA8 rule leaves beyond 1 LSB).
 RGBA8: within 1 LSB per channel for >= 99.99% of pixels, and any pixel beyond
 1 LSB must be margin- or sensitivity-exempt.
+
+The sensitivity costs four more oracle traces per pixel, so it is computed only
+for the pixels that need it (those beyond the plain tolerance and not
+margin-exempt).
 """
 from __future__ import annotations
+
+import json
+import os
 
 import numpy as np
 
@@ -22,17 +32,52 @@ import oracle
 TOL = 1e-4
 MARGIN_REL = 1e-5
 SENS_DELTA = 1e-6
+EXEMPT_SHARE_MAX = 1e-4
+
+
+class LazySensitivity:
+    """The oracle's FP32 sensitivity of a set of pixels, traced on demand."""
+
+    def __init__(self, w, pixels, ref_rgb):
+        self.w = w
+        self.pixels = (oracle.all_pixels(w.params.width, w.params.height) if pixels is None
+                       else np.ascontiguousarray(pixels, np.int32).reshape(-1, 2))
+        self.ref = ref_rgb
+        self.cache: dict[int, float] = {}
+
+    def at(self, idx: np.ndarray) -> np.ndarray:
+        idx = np.asarray(idx, np.int64)
+        todo = np.array([i for i in idx if int(i) not in self.cache], np.int64)
+        if todo.size:
+            px = self.pixels[todo]
+            s = np.zeros(todo.size)
+            for off in ((SENS_DELTA, 0.0), (-SENS_DELTA, 0.0), (0.0, SENS_DELTA), (0.0, -SENS_DELTA)):
+                r2 = oracle.trace(self.w.scene, self.w.camera, self.w.params, px, ndc_offset=off)
+                s = np.maximum(s, np.abs(r2["rgb"] - self.ref[todo]).max(1))
+            self.cache.update(zip(todo.tolist(), s.tolist()))
+        return np.array([self.cache[int(i)] for i in idx], np.float64)
 
 
 def oracle_reference(w, pixels=None, sensitivity=True):
+    """(rgb, margin, sens) of the oracle for the given pixels (None: the frame);
+    sens is traced lazily, only where a comparison needs it."""
     r = oracle.trace(w.scene, w.camera, w.params, pixels, margin=True)
     rgb, margin = r["rgb"], r["margin"]
-    sens = np.zeros(len(rgb))
-    if sensitivity:
-        for off in ((SENS_DELTA, 0.0), (-SENS_DELTA, 0.0), (0.0, SENS_DELTA), (0.0, -SENS_DELTA)):
-            r2 = oracle.trace(w.scene, w.camera, w.params, pixels, ndc_offset=off)
-            sens = np.maximum(sens, np.abs(r2["rgb"] - rgb).max(1))
+    sens = LazySensitivity(w, pixels, rgb) if sensitivity else np.zeros(len(rgb))
     return rgb, margin, sens
+
+
+def _log(kind, stats):
+    """Append one comparison's counts to $RT_PARITY_LOG (JSON lines), if set."""
+    path = os.environ.get("RT_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], "kind": kind,
+                                **stats}) + "\n")
+
+
+def _sens_at(sens, idx):
+    return sens.at(idx) if isinstance(sens, LazySensitivity) else np.asarray(sens, np.float64)[idx]
 
 
 def compare_f32(gpu_rgb, ref_rgb, margin, sens, scene_scale):
@@ -40,17 +85,23 @@ def compare_f32(gpu_rgb, ref_rgb, margin, sens, scene_scale):
     err = np.abs(gpu_rgb - ref_rgb).max(1)
     plain = err <= TOL
     by_margin = margin < MARGIN_REL * scene_scale
-    by_sens = err <= TOL + sens
+    need = np.nonzero(~plain & ~by_margin)[0]
+    by_sens = np.zeros(err.size, bool)
+    if need.size:
+        by_sens[need] = err[need] <= TOL + _sens_at(sens, need)
     ok = plain | by_margin | by_sens
+    n = max(err.size, 1)
     stats = {
         "pixels": int(err.size),
         "max_err": float(err.max()) if err.size else 0.0,
         "frac_within_1e-4": float(plain.mean()) if err.size else 1.0,
+        "plain": int(plain.sum()),
         "margin_exempt": int((~plain & by_margin).sum()),
-        "sensitivity_exempt": int((~plain & ~by_margin & by_sens).sum()),
+        "sensitivity_exempt": int(by_sens.sum()),
+        "exempt_share": float((~plain).sum() - (~ok).sum()) / n,
         "failing": int((~ok).sum()),
-        "max_err_non_exempt": float(err[~(by_margin | (~plain & by_sens))].max()) if err.size else 0.0,
     }
+    _log("f32", stats)
     return ok, stats
 
 
@@ -65,14 +116,21 @@ def compare_rgba8(gpu_words, ref_rgb, margin, sens, scene_scale):
     diff = np.abs(g - r)[:, :3].max(1)
     assert np.all(g[:, 3] == 255)
     within = diff <= 1
-    exempt = (margin < MARGIN_REL * scene_scale) | (sens * 255.0 >= 0.5)
-    ok = within | exempt
+    by_margin = margin < MARGIN_REL * scene_scale
+    need = np.nonzero(~within & ~by_margin)[0]
+    by_sens = np.zeros(diff.size, bool)
+    if need.size:
+        by_sens[need] = _sens_at(sens, need) * 255.0 >= 0.5
+    ok = within | by_margin | by_sens
     stats = {
         "pixels": int(diff.size),
         "frac_within_1lsb": float(within.mean()) if diff.size else 1.0,
         "frac_exact": float((diff == 0).mean()) if diff.size else 1.0,
-        "exempt_beyond_1lsb": int((~within & exempt).sum()),
+        "beyond_1lsb": int((~within).sum()),
+        "margin_exempt_beyond_1lsb": int((~within & by_margin).sum()),
+        "sensitivity_exempt_beyond_1lsb": int(by_sens.sum()),
         "failing": int((~ok).sum()),
         "max_lsb": int(diff.max()) if diff.size else 0,
     }
+    _log("rgba8", stats)
     return ok, stats

@@ -119,7 +119,9 @@ def test_720p_f32_sampled():
 
 def test_4k_area_light_sampled():
     """3840x2160 RGBA8, 256 spheres, 3 point + 1 area light (16 Philox samples),
-    depth 8, rendered in the bench's launch configuration; sampled pixels."""
+    depth 8, through the one-pass kernel (rt_render) at the library's default
+    launch; sampled pixels.  The bench's path (rt_render_ws at the tuned launch)
+    is compared over every pixel in test_fullframe_gpu.py."""
     w = S.area_4k()
     g, ref, margin, sens = sampled(w, 191, 600, S.OUT_RGBA8)
     ok, st = compare_rgba8(g, ref, margin, sens, w.scene.scene_scale)
