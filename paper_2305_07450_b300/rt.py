@@ -467,6 +467,13 @@ def grad_count(dscene: DeviceScene) -> int:
     return int(lib().rt_grad_count(dscene.handle))
 
 
+def backward_workspace_bytes(dscene: DeviceScene, params: scenes.Params, launch=None) -> int:
+    """rt_backward_workspace_bytes: the workspace rt_render_backward needs."""
+    cfg = launch_struct(launch)
+    return int(lib().rt_backward_workspace_bytes(dscene.handle, C.byref(params_struct(params)),
+                                                 C.byref(cfg) if cfg is not None else None))
+
+
 def render_backward(dscene: DeviceScene, camera, params: scenes.Params, dl_dimg: torch.Tensor, *,
                     hitrec: torch.Tensor | None = None, grad: torch.Tensor | None = None,
                     workspace: torch.Tensor | None = None, launch=None, stream=None) -> torch.Tensor:
@@ -491,10 +498,12 @@ def render_backward(dscene: DeviceScene, camera, params: scenes.Params, dl_dimg:
 _UNPACK_INDEX: dict = {}
 
 
-def _unpack_index(n_spheres: int, n_lights: int, device) -> torch.Tensor:
+def _unpack_index(n_spheres: int, n_lights: int, device, coupled: bool = False) -> torch.Tensor:
     """Gather map from the packed gradient (plus one appended zero, index G) to
-    the concatenated records [spheres N x 10 | plane 10 | lights L x 8]."""
-    key = (n_spheres, n_lights, str(device))
+    the concatenated records [spheres N x 10 | plane 10 | lights L x 8].  The
+    packed reflectivity entry goes to the reflectivity field (column 9), or with
+    the coupled reflection ratio to the specular exponent field (column 8)."""
+    key = (n_spheres, n_lights, str(device), bool(coupled))
     idx = _UNPACK_INDEX.get(key)
     if idx is None:
         N, L = n_spheres, n_lights
@@ -503,10 +512,11 @@ def _unpack_index(n_spheres: int, n_lights: int, device) -> torch.Tensor:
         base = 8 * np.arange(N, dtype=np.int64)[:, None]
         sph[:, 0:3] = base + np.array([5, 6, 7])
         sph[:, 4:8] = base + np.array([0, 1, 2, 3])
-        sph[:, 9] = base[:, 0] + 4
+        rcol = 8 if coupled else 9
+        sph[:, rcol] = base[:, 0] + 4
         pl = np.full(10, z, np.int64)
         pl[4:8] = 8 * N + np.arange(4)
-        pl[9] = 8 * N + 4
+        pl[rcol] = 8 * N + 4
         lig = np.full((L, 8), z, np.int64)
         lig[:, 0:4] = 8 * (N + 1) + 4 * np.arange(L, dtype=np.int64)[:, None] + np.arange(4)
         idx = torch.from_numpy(np.concatenate([sph.ravel(), pl, lig.ravel()])).to(device)
@@ -514,13 +524,14 @@ def _unpack_index(n_spheres: int, n_lights: int, device) -> torch.Tensor:
     return idx
 
 
-def unpack_grad(grad: torch.Tensor, n_spheres: int, n_lights: int):
+def unpack_grad(grad: torch.Tensor, n_spheres: int, n_lights: int, coupled: bool = False):
     """Packed gradient -> (spheres [N, 10], plane [10], lights [L, 8]) laid out
     like the scene records (zeros where a field is not differentiated): one
-    gather through a cached index map."""
+    gather through a cached index map (coupled: the render used the coupled
+    reflection ratio, so the reflectivity entry belongs to the exponent field)."""
     N, L = n_spheres, n_lights
     G = 8 * (N + 1) + 4 * L
-    flat = torch.cat([grad[:G], grad.new_zeros(1)])[_unpack_index(N, L, grad.device)]
+    flat = torch.cat([grad[:G], grad.new_zeros(1)])[_unpack_index(N, L, grad.device, coupled)]
     return flat[: 10 * N].view(N, 10), flat[10 * N: 10 * N + 10], flat[10 * N + 10:].view(L, 8)
 
 
@@ -548,7 +559,7 @@ class RenderFn(torch.autograd.Function):
         ds = ctx.dscene
         ds.update(spheres=sph, plane=pl if ds.has_plane else None, lights=lig)
         g = render_backward(ds, ctx.camera, ctx.params, grad_img.float(), hitrec=hr)
-        gs, gp, gl = unpack_grad(g, ds.n_spheres, ds.n_lights)
+        gs, gp, gl = unpack_grad(g, ds.n_spheres, ds.n_lights, coupled=bool(ctx.params.refl_coupled))
         return gs, gp, gl, None, None, None
 
 
