@@ -357,7 +357,12 @@ size_t rt_scene_bytes(const rt_scene *scene);
  * silhouette or shadow-edge terms), for inverse rendering.  Not in the paper.
  * Gradient layout (floats): sphere i at 8i + {albedo r, g, b, k_s, reflectivity,
  * centre x, y, z}; the plane at 8N + {albedo r, g, b, k_s, reflectivity, 0, 0,
- * 0}; light l at 8(N + 1) + 4l + {position x, y, z, intensity}. */
+ * 0}; light l at 8(N + 1) + 4l + {position x, y, z, intensity}.  The
+ * "reflectivity" entry is the derivative with respect to the field that sets the
+ * reflection ratio: the reflectivity record field, or, with refl_coupled (the
+ * paper's ratio = exponent / MAX_REFLECTIVITY capped at 1, Section 3.7), the
+ * specular exponent field, including the exponent's effect on the specular terms.
+ * Scenes with a sky panorama are refused (RT_ERR_UNSUPPORTED). */
 
 /* Number of floats of the packed gradient: 8 (N + 1) + 4 L. */
 size_t rt_grad_count(const rt_scene *scene);

@@ -126,7 +126,8 @@ constexpr size_t kWsEntryBytes = 64;
 static_assert(sizeof(WsCtl) <= kWsCtlBytes, "workspace control block");
 
 __host__ __device__ inline unsigned ws_cap(size_t bytes) {
-    return bytes <= kWsCtlBytes ? 0u : (unsigned)std::min<size_t>((bytes - kWsCtlBytes) / (2 * kWsEntryBytes), 1u << 30);
+    const size_t n = bytes <= kWsCtlBytes ? 0 : (bytes - kWsCtlBytes) / (2 * kWsEntryBytes);
+    return (unsigned)(n < (size_t(1) << 30) ? n : (size_t(1) << 30));
 }
 __device__ __forceinline__ PathQueue ws_queue(unsigned char* ws, unsigned cap, int k) {
     WsCtl* c = reinterpret_cast<WsCtl*>(ws);
@@ -627,9 +628,15 @@ rt_status ensure_smem(K kernel, size_t bytes) {
 struct BatchPlanHost {
     std::vector<unsigned char> table;  // workspace image: head, frames, items
     int n_items = 0;
+    int n_filt = 0;  // the first n_filt items: frames rendered with the line filter
     size_t smem = 0;
     bool chunked = false;
 };
+
+// The shading path a frame of a batch takes: the line filter (with the cone
+// passes) from kFilterMinPad spheres on, as rt_render does, unless the batch stages
+// its tables chunk by chunk.
+bool batch_filtered(const rt_scene* s, bool chunked) { return !chunked && s->ns_pad >= kFilterMinPad; }
 
 // Relative cost of one tile of a frame, for the longest-first item order.
 double tile_cost(const rt_scene* s, const rt_render_params* p) {
@@ -676,12 +683,18 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
         n_items += t;
     }
     if (n_items >= (1ll << 31)) return RT_ERR_UNSUPPORTED;
-    // longest-first: frames by estimated tile cost, tiles of a frame in raster order
+    // the line-filter frames first, then the others; each class longest-first (frames
+    // by estimated tile cost, tiles of a frame in raster order)
     std::vector<int> order((size_t)n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const bool fa = batch_filtered(scenes[a], chunked), fb = batch_filtered(scenes[b], chunked);
+        if (fa != fb) return fa;
         return tile_cost(scenes[a], &params[a]) > tile_cost(scenes[b], &params[b]);
     });
+    long long n_filt = 0;
+    for (int i = 0; i < n; ++i)
+        if (batch_filtered(scenes[i], chunked)) n_filt += tiles[(size_t)i];
     const size_t items_off = batch_items_offset(n);
     plan->table.assign(items_off + (size_t)n_items * 4, 0);
     std::memcpy(plan->table.data() + batch_frames_offset(), frames.data(), (size_t)n * sizeof(BatchFrame));
@@ -690,46 +703,65 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
     for (int f : order)
         for (int t = 0; t < tiles[(size_t)f]; ++t) items[k++] = ((uint32_t)f << kItemTileBits) | (uint32_t)t;
     plan->n_items = (int)n_items;
+    plan->n_filt = (int)n_filt;
     plan->smem = smem;
     plan->chunked = chunked;
     return RT_OK;
 }
 
-rt_status batch_grid(const Launch& L, size_t smem, bool chunked, int* grid) {
-    int dev = 0, sms = 0, per_sm = 0;
+// Resident CTAs of the batch kernel instances: grid[0] for the segment-test
+// instance, grid[1] for the line-filter one.
+rt_status batch_grid(const Launch& L, size_t smem, bool chunked, int grid[2]) {
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
-    if (L.min_blocks > 0) {
-        per_sm = L.min_blocks;
-    } else {
-        e = chunked ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<true>, L.bx * L.by, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<false>, L.bx * L.by, smem);
+    for (int fm = 0; fm < 2; ++fm) {
+        int per_sm = 0;
+        if (L.min_blocks > 0) {
+            per_sm = L.min_blocks;
+        } else if (chunked) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<true, 0>, L.bx * L.by, smem);
+        } else {
+            e = fm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<false, 1>, L.bx * L.by, smem)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<false, 0>, L.bx * L.by, smem);
+        }
         if (e != cudaSuccess) return cuda_status(e);
+        grid[fm] = sms * std::max(per_sm, 1);
     }
-    *grid = sms * std::max(per_sm, 1);
     return RT_OK;
 }
 
 }  // namespace
 
 rt_status batch_smem(bool chunked, size_t smem) {
-    return chunked ? ensure_smem(rt_batch_kernel<true>, smem) : ensure_smem(rt_batch_kernel<false>, smem);
+    if (chunked) return ensure_smem(rt_batch_kernel<true, 0>, smem);
+    rt_status st = ensure_smem(rt_batch_kernel<false, 0>, smem);
+    return st != RT_OK ? st : ensure_smem(rt_batch_kernel<false, 1>, smem);
 }
 
-void batch_launch(bool chunked, int grid, const Launch& L, size_t smem, cudaStream_t st, unsigned char* ws, int n,
-                  int n_items) {
+// The line-filter instance over items [0, n_filt), then the segment-test instance
+// over [n_filt, n_items), in stream order; an empty class launches nothing.
+void batch_launch(bool chunked, const int grid[2], const Launch& L, size_t smem, cudaStream_t st, unsigned char* ws,
+                  int n, int n_items, int n_filt) {
     const dim3 block(32, (L.bx * L.by) / 32);
     const int hstage = L.staging == 2 ? 2 : 1;
-    if (chunked)
-        rt_batch_kernel<true><<<grid, block, smem, st>>>(ws, n, n_items, hstage, L.bx, L.by);
-    else
-        rt_batch_kernel<false><<<grid, block, smem, st>>>(ws, n, n_items, hstage, L.bx, L.by);
+    if (n_filt > 0)
+        rt_batch_kernel<false, 1><<<grid[1], block, smem, st>>>(ws, n, 0, n_filt, hstage, L.bx, L.by);
+    if (n_items > n_filt) {
+        if (chunked)
+            rt_batch_kernel<true, 0><<<grid[0], block, smem, st>>>(ws, n, n_filt, n_items - n_filt, hstage, L.bx,
+                                                                   L.by);
+        else
+            rt_batch_kernel<false, 0><<<grid[0], block, smem, st>>>(ws, n, n_filt, n_items - n_filt, hstage, L.bx,
+                                                                    L.by);
+    }
 }
 
 struct rt_batch {
     bool chunked = false;
-    int n = 0, n_items = 0, grid = 0;
+    int n = 0, n_items = 0, n_filt = 0;
+    int grid[2] = {0, 0};
     Launch L{};
     size_t smem = 0, ws_bytes = 0;
     void* ws = nullptr;
@@ -1152,14 +1184,15 @@ rt_status rt_render_batch(int32_t n, const rt_scene* const* scenes, const rt_cam
     if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) || workspace_bytes < plan.table.size())
         return RT_ERR_INVALID_ARG;
     if ((st = batch_smem(plan.chunked, plan.smem)) != RT_OK) return st;
-    int grid = 0;
-    if ((st = batch_grid(L, plan.smem, plan.chunked, &grid)) != RT_OK) return st;
+    int grid[2] = {0, 0};
+    if ((st = batch_grid(L, plan.smem, plan.chunked, grid)) != RT_OK) return st;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     // pageable source: the runtime stages it before returning, so the vector may go
     cudaError_t e = cudaMemcpyAsync(workspace_dev, plan.table.data(), plan.table.size(), cudaMemcpyHostToDevice, st_);
     if (e != cudaSuccess) return cuda_status(e);
-    batch_launch(plan.chunked, grid, L, plan.smem, st_, static_cast<unsigned char*>(workspace_dev), n, plan.n_items);
-    g_launches++;
+    batch_launch(plan.chunked, grid, L, plan.smem, st_, static_cast<unsigned char*>(workspace_dev), n, plan.n_items,
+                 plan.n_filt);
+    g_launches += (plan.n_filt > 0) + (plan.n_items > plan.n_filt);
     return cuda_status(cudaGetLastError());
 }
 
@@ -1192,10 +1225,11 @@ rt_status rt_batch_create(int32_t n, const rt_scene* const* scenes, const rt_cam
     b->chunked = plan.chunked;
     b->n = n;
     b->n_items = plan.n_items;
+    b->n_filt = plan.n_filt;
     b->L = L;
     b->smem = plan.smem;
     b->ws_bytes = plan.table.size();
-    if ((st = batch_grid(L, plan.smem, plan.chunked, &b->grid)) != RT_OK) {
+    if ((st = batch_grid(L, plan.smem, plan.chunked, b->grid)) != RT_OK) {
         rt_batch_free(b);
         return st;
     }
@@ -1209,11 +1243,12 @@ rt_status rt_batch_create(int32_t n, const rt_scene* const* scenes, const rt_cam
         e = cudaMemcpyAsync(b->ws, b->pinned, b->ws_bytes, cudaMemcpyHostToDevice, st_);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->ready, st_);
-    // graph: reset the work counter, then the persistent kernel
+    // graph: reset the two work counters, then the persistent kernel instances
     if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(b->ws, 0, sizeof(unsigned), b->cap);
-        batch_launch(b->chunked, b->grid, L, b->smem, b->cap, static_cast<unsigned char*>(b->ws), n, b->n_items);
+        cudaMemsetAsync(b->ws, 0, 2 * sizeof(unsigned), b->cap);
+        batch_launch(b->chunked, b->grid, L, b->smem, b->cap, static_cast<unsigned char*>(b->ws), n, b->n_items,
+                     b->n_filt);
         cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = e2;
@@ -1232,7 +1267,7 @@ rt_status rt_batch_launch(rt_batch* b, void* stream) {
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamWaitEvent(st_, b->ready, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st_);
-    if (e == cudaSuccess) g_launches++;
+    if (e == cudaSuccess) g_launches += (b->n_filt > 0) + (b->n_items > b->n_filt);
     return cuda_status(e);
 }
 
@@ -1252,7 +1287,7 @@ rt_status rt_render_backward(const rt_scene* s, const rt_camera* cam, const rt_r
     rt_status st = validate_params(s, p);
     if (st != RT_OK) return st;
     if ((st = validate_camera(cam)) != RT_OK) return st;
-    if (p->refl_coupled || s->sky_dev) return RT_ERR_UNSUPPORTED;
+    if (s->sky_dev) return RT_ERR_UNSUPPORTED;
     if (!dl_dimg_dev || (reinterpret_cast<uintptr_t>(dl_dimg_dev) & 15) || dl_pitch_bytes < (size_t)p->width * 16 ||
         (dl_pitch_bytes & 15) || !grad_dev || (hitrec_dev && (reinterpret_cast<uintptr_t>(hitrec_dev) & 3)))
         return RT_ERR_INVALID_ARG;
@@ -1338,18 +1373,19 @@ void* g_noalloc_dev_ptr[kMaxDevices] = {};
 alignas(256) unsigned char g_noalloc_host[RT_NOALLOC_SCRATCH_BYTES];
 
 // The workspace image of rt_render_batch, written into a fixed buffer without any
-// heap use (frames in longest-first order by tile cost, tiles in raster order).
+// heap use (line-filter frames first, each class in longest-first order by tile
+// cost, tiles in raster order).
 rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera* cams,
                            const rt_render_params* params, void* const* outs, const size_t* pitches,
                            const Launch& L, unsigned char* buf, size_t cap, size_t* bytes, int* n_items_out,
-                           size_t* smem_out, bool* chunked_out) {
+                           int* n_filt_out, size_t* smem_out, bool* chunked_out) {
     if (n < 1 || !scenes || !cams || !params || !outs || !pitches) return RT_ERR_INVALID_ARG;
     if (L.bx * L.by > kBatchMaxThreads) return RT_ERR_INVALID_ARG;
     if (L.accel) return RT_ERR_UNSUPPORTED;
     if (n > RT_NOALLOC_MAX_FRAMES) return RT_ERR_EXCEEDS_SCRATCH;
     int order[RT_NOALLOC_MAX_FRAMES];
     int tiles[RT_NOALLOC_MAX_FRAMES];
-    long long n_items = 0;
+    long long n_items = 0, n_filt = 0;
     const size_t items_off = batch_items_offset(n);
     if (items_off > cap) return RT_ERR_EXCEEDS_SCRATCH;
     std::memset(buf, 0, items_off);  // the work counter starts at zero
@@ -1378,10 +1414,16 @@ rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera
         if (t >= (1ll << kItemTileBits)) return RT_ERR_UNSUPPORTED;
         tiles[i] = (int)t;
         n_items += t;
-        // insertion into the longest-first order (stable: ties keep input order)
+        const bool filt = batch_filtered(s, chunked);
+        if (filt) n_filt += t;
+        // insertion into the order of rt_render_batch: line-filter frames first, each
+        // class longest-first (stable: ties keep input order)
         const double c = tile_cost(s, p);
         int j = i;
-        while (j > 0 && tile_cost(scenes[order[j - 1]], &params[order[j - 1]]) < c) {
+        while (j > 0) {
+            const int q = order[j - 1];
+            const bool fq = batch_filtered(scenes[q], chunked);
+            if (!(filt && !fq) && !(filt == fq && tile_cost(scenes[q], &params[q]) < c)) break;
             order[j] = order[j - 1];
             --j;
         }
@@ -1397,6 +1439,7 @@ rt_status batch_pack_fixed(int n, const rt_scene* const* scenes, const rt_camera
     }
     *bytes = total;
     *n_items_out = (int)n_items;
+    *n_filt_out = (int)n_filt;
     *smem_out = stage_smem_bytes(chunked, max_pad, (L.bx * L.by) / 32);
     *chunked_out = chunked;
     return RT_OK;
@@ -1430,19 +1473,20 @@ extern "C" rt_status rt_render_batch_noalloc(int32_t n, const rt_scene* const* s
         g_noalloc_dev_ptr[dev] = ptr;
     }
     size_t bytes = 0, smem = 0;
-    int n_items = 0;
+    int n_items = 0, n_filt = 0;
     bool chunked = false;
     st = batch_pack_fixed(n, scenes, cams, params, outs_dev, pitches, L, g_noalloc_host, sizeof(g_noalloc_host),
-                          &bytes, &n_items, &smem, &chunked);
+                          &bytes, &n_items, &n_filt, &smem, &chunked);
     if (st != RT_OK) return st;
     if ((st = batch_smem(chunked, smem)) != RT_OK) return st;
-    int grid = 0;
-    if ((st = batch_grid(L, smem, chunked, &grid)) != RT_OK) return st;
+    int grid[2] = {0, 0};
+    if ((st = batch_grid(L, smem, chunked, grid)) != RT_OK) return st;
     // pageable source: staged by the runtime before the call returns, so the static
     // host image is free for the next call
     e = cudaMemcpyAsync(g_noalloc_dev_ptr[dev], g_noalloc_host, bytes, cudaMemcpyHostToDevice, st_);
     if (e != cudaSuccess) return cuda_status(e);
-    batch_launch(chunked, grid, L, smem, st_, static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]), n, n_items);
-    g_launches++;
+    batch_launch(chunked, grid, L, smem, st_, static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]), n, n_items,
+                 n_filt);
+    g_launches += (n_filt > 0) + (n_items > n_filt);
     return cuda_status(cudaGetLastError());
 }

@@ -15,7 +15,11 @@
 //
 // Gradient layout (floats): sphere i at 8i + {albedo r, g, b, k_s, reflectivity,
 // centre x, y, z}; the plane at 8N + {albedo r, g, b, k_s, reflectivity, 0, 0, 0};
-// light l at 8(N + 1) + 4l + {position x, y, z, intensity}.
+// light l at 8(N + 1) + 4l + {position x, y, z, intensity}.  "Reflectivity" is the
+// field that sets the reflection ratio: rho itself, or -- with the paper's coupling
+// of Section 3.7, rho = min(e / MAX_REFLECTIVITY, 1) -- the specular exponent e,
+// whose gradient then also carries its effect on the specular terms
+// (d(x^e)/de = x^e ln x).
 //
 // Reduction (deterministic): within a warp, lanes that hit the same primitive are
 // summed by a fixed butterfly and the group's first lane adds the sum to the
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             Tt[k] = T;
             const int id = __float_as_int(rec[k * kRecStride]);
             const float t = rec[k * kRecStride + 1];
-            const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t, 0.0f);
+            const HitGeom hg = hit_geometry<CH>(sc, id, o, o_lo, d, t, fr.refl_inv_max);
             float A = fr.ka;
             for (int li = 0; li < nl; ++li) {
                 const float4 Lp = h.light_p[li];
@@ -160,6 +164,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
     f3 Rn = mk3(0.f, 0.f, 0.f);                     // R_{k+1}
     f3 Ob = mk3(0.f, 0.f, 0.f), Db = mk3(0.f, 0.f, 0.f);  // adjoint of ray k+1
     const int Kw = (int)__reduce_max_sync(0xffffffffu, (unsigned)K);
+    const bool coupled = fr.refl_inv_max > 0.0f;
     for (int k = Kw - 1; k >= 0; --k) {
         float pg[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int pid = -1;
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             const int id = __float_as_int(rec[k * kRecStride]);
             const float t = rec[k * kRecStride + 1];
             const f3 d = Dd[k];
-            const HitGeom hg = hit_geometry<CH>(sc, id, Oh[k], Ol[k], d, t, 0.0f);
+            const HitGeom hg = hit_geometry<CH>(sc, id, Oh[k], Ol[k], d, t, fr.refl_inv_max);
             const f3 n = hg.n;
             const f3 alb = mk3(hg.m.x, hg.m.y, hg.m.z);
             const float ks = hg.m.w, ex = hg.m2.x, rho = hg.m2.y;
@@ -178,6 +183,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             const float Ab = dot(Rb, last ? scl(alb, beta) : add(scl(alb, beta), scl(Rn, rho)));
             const float Sb = Rb.x + Rb.y + Rb.z;
             f3 pb = mk3(0.f, 0.f, 0.f), nb = mk3(0.f, 0.f, 0.f), db = mk3(0.f, 0.f, 0.f);
+            float exb = 0.0f;  // adjoint of the exponent through the specular terms (coupled mode)
             // lights, one pass: the forward sums A and S (light order, as the forward
             // pass forms them) and their adjoints
             float A = fr.ka, S = 0.0f;
@@ -203,6 +209,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
                     const f3 r = sub(scl(n, 2.0f * ndl), lh);
                     const float vr = -dot(d, r);
                     if (vr > 0.0f && sp > 0.0f) {
+                        if (coupled) exb = fmaf(spb * sp, logf(vr), exb);
                         const float vrb = spb * ex * sp / vr;
                         db = fma3(r, -vrb, db);
                         const f3 rb = scl(d, -vrb);
@@ -215,6 +222,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
                     const f3 hv = normalize_rn(sub(lh, d), &ulen);
                     const float nh = dot(n, hv);
                     if (nh > 0.0f && sp > 0.0f) {
+                        if (coupled) exb = fmaf(spb * sp, logf(nh), exb);
                         const float nhb = spb * ex * sp / nh;
                         nb = fma3(hv, nhb, nb);
                         const f3 hb = scl(n, nhb);
@@ -236,7 +244,10 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             pg[0] = beta * A * Rb.x;
             pg[1] = beta * A * Rb.y;
             pg[2] = beta * A * Rb.z;
-            pg[4] = last ? 0.0f : dot(Rb, sub(scl(Rn, A), scl(alb, A)));
+            const float rhob = last ? 0.0f : dot(Rb, sub(scl(Rn, A), scl(alb, A)));
+            // coupled: rho = min(e / MAX_REFLECTIVITY, 1) has slope 1 / MAX_REFLECTIVITY
+            // below the cap and 0 at it
+            pg[4] = coupled ? fmaf(ex * fr.refl_inv_max < 1.0f ? fr.refl_inv_max : 0.0f, rhob, exb) : rhob;
             // the ray that left this hit: origin p + eps n, direction d - 2 (d.n) n
             if (!last) {
                 pb = add(pb, Ob);
