@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # square roots, reciprocals and exp2/log2 are MUFU work and not counted).
 FLOPS = {
     "closest_sphere_tests": 17,   # oc (3), b' = oc.d (5), c' = oc.oc - r^2 (7), disc (2)
-    "closest_plane_tests": 12,    # d.n (5), o.n + d (6), t (1)
+    "closest_plane_tests": 12,    # general plane n.x + d = 0: d.n (5), o.n + d (6), t = num * rcp (1)
     "shadow_sphere_tests": 17,
     "shadow_plane_tests": 12,
     "primary_rays": 20,           # NDC (4), u R + v U + b F (12), normalise (4)

@@ -67,28 +67,94 @@ def fd(w, px, wt, where, field, idx):
     return (lp - lm) / (vp - vm)
 
 
-def test_adjoint_matches_oracle_finite_differences():
-    w = small_diff_workload()
-    px, wt, wimg = safe_weights(w)
-    assert len(px) > 2000
-    g = gpu_grad(w, wimg)
+def fd_checks(w, g):
+    """Every differentiated parameter: (record, field, index, packed entry)."""
     N, L = w.scene.n_spheres, w.scene.n_lights
-    # the spheres that matter most to this loss, every field; the plane; every light
-    mag = np.abs(g[: 8 * N].reshape(N, 8)).sum(1)
+    rfield = 8 if w.params.refl_coupled else 9     # the field that sets the reflection ratio
     checks = []
-    for i in np.argsort(-mag)[:5]:
-        for f_rec, f_g in ((4, 0), (5, 1), (6, 2), (7, 3), (9, 4), (0, 5), (1, 6), (2, 7)):
-            checks.append(("sphere", f_rec, int(i), 8 * int(i) + f_g))
-    for f_rec, f_g in ((4, 0), (5, 1), (6, 2), (7, 3), (9, 4)):
+    for i in range(N):
+        for f_rec, f_g in ((4, 0), (5, 1), (6, 2), (7, 3), (rfield, 4), (0, 5), (1, 6), (2, 7)):
+            checks.append(("sphere", f_rec, i, 8 * i + f_g))
+    for f_rec, f_g in ((4, 0), (5, 1), (6, 2), (7, 3), (rfield, 4)):
         checks.append(("plane", f_rec, 0, 8 * N + f_g))
     for l in range(L):
         for c in range(4):
             checks.append(("light", c, l, 8 * (N + 1) + 4 * l + c))
+    return checks
+
+
+def fd_pixels(w, px, wt, where, field, idx, h_scale=1.0):
+    """Per-pixel contributions to the central difference of the oracle loss in one
+    FP32 record field (step 16 FP32 ulps of the value, times h_scale)."""
+    sc = w.scene
+    arr = {"sphere": sc.spheres, "plane": sc.plane, "light": sc.lights}[where]
+    pos = (idx, field) if where != "plane" else (field,)
+    v = float(arr[pos])
+    h = max(16.0 * abs(float(np.spacing(np.float32(v)))), 1e-7) * h_scale
+    cols = []
+    for sgn in (1, -1):
+        new = S.Scene(spheres=sc.spheres.copy(), plane=sc.plane.copy(), lights=sc.lights.copy(), scale=sc.scale)
+        a = {"sphere": new.spheres, "plane": new.plane, "light": new.lights}[where]
+        a[pos] = np.float32(v + sgn * h)
+        cols.append((float(a[pos]), oracle.trace(new, w.camera, w.params, px)["rgb"]))
+    (vp, rp), (vm, rm) = cols
+    return ((rp - rm) * wt).sum(1) / (vp - vm)
+
+
+def check_against_fd(w):
+    """Every parameter's adjoint against the oracle's central difference over the
+    pixels whose margin exceeds 1e-3 x scene scale.  Visibility is held fixed in the
+    adjoint, so a pixel counts only where the oracle colour is smooth at the step's
+    scale: reflection chains amplify a parameter step until a later bounce's shadow
+    edge or silhouette is crossed even at large margins, and there the central
+    differences at steps h and h/2 disagree.  Such pixels (the union over all
+    parameters) get zero loss weight in both the adjoint and the difference."""
+    px, wt, _ = safe_weights(w)
+    checks = fd_checks(w, None)
+    totals, flagged = [], set()
+    for where, f, i, _ in checks:
+        c1 = fd_pixels(w, px, wt, where, f, i)
+        c2 = fd_pixels(w, px, wt, where, f, i, 0.5)
+        rough = np.abs(c1 - c2) > 0.05 * np.maximum(np.abs(c1), np.abs(c2)) + 1e-6
+        flagged.update(np.nonzero(rough)[0].tolist())
+        totals.append(c1)
+    U = np.array(sorted(flagged), np.int64)
+    want = np.array([c.sum() - c[U].sum() for c in totals])
+    wt2 = wt.copy()
+    wt2[U] = 0.0
+    wimg = np.zeros((w.params.height, w.params.width, 3))
+    wimg[px[:, 1], px[:, 0]] = wt2
+    g = gpu_grad(w, wimg)
     got = np.array([g[j] for *_, j in checks])
-    want = np.array([fd(w, px, wt, where, f, i) for where, f, i, _ in checks])
     scale = np.abs(want).max()
     bad = np.abs(got - want) > 2e-3 * np.abs(want) + 2e-4 * scale
+    print(f"{len(checks)} parameters, {len(px)} pixels ({len(U)} not smooth at the step's scale), max rel err "
+          f"{float((np.abs(got - want) / (np.abs(want) + 1e-3 * scale)).max()):.2e}")
+    assert len(U) <= 1e-3 * len(px), len(U)
     assert not bad.any(), [(checks[k], got[k], want[k]) for k in np.nonzero(bad)[0]]
+
+
+def test_adjoint_matches_oracle_finite_differences():
+    """The 512x512 differentiable workload (32 spheres + plane, 2 lights, bounce
+    limit 2), every pixel whose margin exceeds 1e-3 x scene scale: every
+    parameter of every sphere, of the plane and of every light."""
+    w = S.diff_512()
+    check_against_fd(w)
+
+
+def test_adjoint_coupled_reflectivity_matches_finite_differences():
+    """The paper's coupled reflection ratio (Section 3.7: ratio = exponent /
+    MAX_REFLECTIVITY, capped at 1), Blinn-Phong, bounce limit 2 on the 512x512
+    scene: the reflectivity entry is the derivative with respect to the exponent
+    field, through the ratio and the specular terms.  MAX_REFLECTIVITY 40 puts the
+    exponent 32 below the cap; the plane's exponent is raised above it so that the
+    capped branch is checked too."""
+    w = S.diff_512()
+    w.params.refl_coupled, w.params.max_reflectivity = 1, 40.0
+    w.params.shading_model = S.BLINN_PHONG
+    w.scene.plane = w.scene.plane.copy()
+    w.scene.plane[8] = np.float32(48.0)
+    check_against_fd(w)
 
 
 def test_adjoint_closed_form_single_sphere():
@@ -150,13 +216,32 @@ def test_inverse_rendering_reduces_loss_and_parameter_error(tmp_path):
     assert len(out2["history"]) == 110 and out2["history"][99] == h[99]
 
 
-def test_backward_refuses_the_coupled_mode():
+def test_inverse_loop_graph_equals_eager_steps():
+    """The captured step replayed k times gives the parameters, Adam moments and
+    loss history of the same step run k times eagerly, bit for bit."""
+    w = small_diff_workload(96, 64)
+    truth = S.perturbed_target(w)
+    tgt = inverse.target_image(truth, w)
+    a = inverse.InverseLoop(w, tgt, 9, 0.05, graph=True)
+    b = inverse.InverseLoop(w, tgt, 9, 0.05, graph=False)
+    a.run(9)
+    b.run(9)
+    torch.cuda.synchronize()
+    for name in ("theta", "m", "v", "t", "hist"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+    assert int(a.k.item()) == 9 and float(a.hist[8]) < float(a.hist[0])
+    a.close()
+    b.close()
+
+
+def test_backward_refuses_a_sky():
     w = small_diff_workload(32, 32)
-    w.params.refl_coupled, w.params.max_reflectivity = 1, 64.0
     ds = rt.DeviceScene(w.scene)
+    ds.set_sky(S.sky_texture(1, 64, 32))
     dl = torch.zeros((32, 32, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(rt.RtError):
         rt.render_backward(ds, w.camera, w.params, dl)
+    ds.close()
 
 
 @pytest.mark.parametrize("W,H", [(264, 200), (96, 40)])
