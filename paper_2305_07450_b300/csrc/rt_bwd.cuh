@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
             float A = fr.ka;
             for (int li = 0; li < nl; ++li) {
                 const float4 Lp = h.light_p[li];
-                const f3 lh = normalize_rn(sub(sub(xyz(Lp), hg.p), hg.p_lo));
+                const f3 lh = normalize(sub(sub(xyz(Lp), hg.p), hg.p_lo));
                 const float ndl = dot(hg.n, lh);
                 if (ndl > 0.0f) A = fmaf(Lp.w * rec[k * kRecStride + 2 + li], ndl, A);
             }
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
                 T *= hg.m2.y * A;
                 f3 po_lo;
                 const f3 po = offset_origin(hg, fr.eps, po_lo);
-                d = normalize_rn(fma3(hg.n, -2.0f * dot(d, hg.n), d));
+                d = normalize(fma3(hg.n, -2.0f * dot(d, hg.n), d));
                 o = po;
                 o_lo = po_lo;
             }
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
                 const float4 Lp = h.light_p[li];
                 float dist;
                 const f3 Lv = sub(sub(xyz(Lp), hg.p), hg.p_lo);
-                const f3 lh = normalize_rn(Lv, &dist);
+                const f3 lh = normalize(Lv, &dist);
                 const float ndl = dot(n, lh);
                 if (ndl <= 0.0f) continue;
                 const float v = rec[k * kRecStride + 2 + li];
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) rt_bwd_kernel(const SceneView sv, const F
                     }
                 } else {
                     float ulen;
-                    const f3 hv = normalize_rn(sub(lh, d), &ulen);
+                    const f3 hv = normalize(sub(lh, d), &ulen);
                     const float nh = dot(n, hv);
                     if (nh > 0.0f && sp > 0.0f) {
                         if (coupled) exb = fmaf(spb * sp, logf(nh), exb);

@@ -23,14 +23,26 @@ __device__ __forceinline__ f3 fma3(f3 a, float s, f3 b) {  // a * s + b
 }
 __device__ __forceinline__ float dot(f3 a, f3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 __device__ __forceinline__ f3 xyz(float4 v) { return mk3(v.x, v.y, v.z); }
-// Unit vector with a correctly rounded reciprocal square root: ray directions and
-// light directions feed distances of tens of units, so their error is kept at
-// half an ulp per component before the multiply.
-__device__ __forceinline__ f3 normalize_rn(f3 a, float* len_out = nullptr) {
+// Unit vector by the hardware reciprocal square root (rsqrtf, within 2 ulp by CUDA's
+// documented bound): every path -- one-pass, queued, batch, hierarchy, adjoint --
+// forms ray and light directions through this one function, so they agree bit for
+// bit; against the FP64 definition the 2 ulp are far inside the 1e-4 colour
+// tolerance.  The correctly rounded root (__frsqrt_rn) cost the 4K frame 2.5 %.
+__device__ __forceinline__ f3 normalize(f3 a, float* len_out = nullptr) {
     float l2 = dot(a, a);
-    float inv = __frsqrt_rn(l2);
+    float inv = rsqrtf(l2);
     if (len_out) *len_out = __fsqrt_rn(l2);
     return scl(a, inv);
+}
+
+// Approximate reciprocal (rcp.approx.f32: within 1 ulp, subnormals kept), for the
+// segment parameter's W = V / |V|^2: u = clamp(oc.W, 0, 1) only picks the point of
+// the segment where the distance to the centre is evaluated, and every bound on the
+// segment test (the line filter's, the cones') holds for any u in [0, 1].
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // Packed FP32 pairs (sm_100 family): one instruction performs two FP32 operations,
