@@ -35,6 +35,11 @@ __device__ __forceinline__ f3 normalize(f3 a, float* len_out = nullptr) {
     return scl(a, inv);
 }
 
+// Square root for the culling passes' bounds: x * rsqrtf(x), within 3 ulp (every
+// bound it enters carries at least 2^-18 of relative slack); 0 for x = 0; NaN for
+// NaN and +inf, which the callers' range checks take as "no bound".
+__device__ __forceinline__ float sqrt_bound(float x) { return x == 0.0f ? 0.0f : x * rsqrtf(x); }
+
 // Approximate reciprocal (rcp.approx.f32: within 1 ulp, subnormals kept), for the
 // segment parameter's W = V / |V|^2: u = clamp(oc.W, 0, 1) only picks the point of
 // the segment where the distance to the centre is evaluated, and every bound on the

@@ -472,11 +472,11 @@ __device__ __noinline__ bool ray_cull(const float4* __restrict__ geo, int n, uns
     const f3 dp = sub(o, p0);
     // warp minimum / maxima (non-negative floats order as their bits)
     const float kw = __uint_as_float(__reduce_min_sync(mask, __float_as_uint(k >= 0.5f ? k : 0.0f))) - 0x1p-18f;
-    const float om = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(sqrtf(dot(o, o)))));
-    const float dm = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(sqrtf(dot(dp, dp)))));
+    const float om = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(sqrt_bound(dot(o, o)))));
+    const float dm = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(sqrt_bound(dot(dp, dp)))));
     const float rho = (r_max + 0x1p-16f * (c_max + om) + dm) * (1.0f + 0x1p-16f);
     if (!(kw >= 0.5f && rho <= 0x1p30f)) return false;
-    const float sw = sqrtf(fmaxf(fmaf(-kw, kw, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
+    const float sw = sqrt_bound(fmaxf(fmaf(-kw, kw, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
     const int nb = n / kPad;
     const int rank = __popc(mask & ((1u << lane) - 1u)), cnt = __popc(mask);
     for (int w = rank; w < (nb + 31) / 32; w += cnt) cw[w] = 0u;
@@ -525,20 +525,20 @@ __device__ __noinline__ bool point_pass(const float4* __restrict__ geo, int n, u
             k = dot(a, dir);
             k = k >= 0.5f ? k : 0.0f;  // NaN: 0
             const f3 E = sub(add(po, sub(sub(L, p), p_lo)), L);  // po + V - L, V as the set-up forms it
-            e = sqrtf(dot(E, E));
+            e = sqrt_bound(dot(E, E));
             const f3 D = sub(po, L);
-            dd = sqrtf(dot(D, D));
+            dd = sqrt_bound(dot(D, D));
         }
         // warp minimum / maxima (non-negative floats order as their bits)
         const float kw = __uint_as_float(__reduce_min_sync(mask, __float_as_uint(k))) - 0x1p-18f;
         const float em = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(e)));
         const float dm = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(dd)));
-        const float rl = (rho + em + 0x1p-16f * (sqrtf(dot(L, L)) + dm)) * (1.0f + 0x1p-15f);
+        const float rl = (rho + em + 0x1p-16f * (sqrt_bound(dot(L, L)) + dm)) * (1.0f + 0x1p-15f);
         if (!(kw >= 0.5f && rl <= 0x1p30f)) {
             ok = false;
             break;
         }
-        const float sw = sqrtf(fmaxf(fmaf(-kw, kw, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
+        const float sw = sqrt_bound(fmaxf(fmaf(-kw, kw, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
         const RayPair o2 = ray_pair(L);
         const float2 ax = dup2(a.x), ay = dup2(a.y), az = dup2(a.z);
         const float2 c0 = dup2(-fmaf(kw, kw, -0x1p-16f)), tw = dup2(2.0f * rl * sw);
@@ -1068,7 +1068,7 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
             }
         } else {
             const float sr = Ls.y * ri * (1.0f + 0x1p-20f);  // >= R / dist
-            kap = sqrtf(fmaxf(fmaf(-sr, sr, 1.0f), 0.0f));
+            kap = sqrt_bound(fmaxf(fmaf(-sr, sr, 1.0f), 0.0f));
         }
         kap -= 0x1p-17f;
         cone_ok = kap >= 0.5f;  // NaN: false
@@ -1086,25 +1086,25 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         const f3 aw = mk3(__shfl_sync(mask, ax.x, ld), __shfl_sync(mask, ax.y, ld), __shfl_sync(mask, ax.z, ld));
         cone_ok = cone_ok && lc == lw;
         cm = __ballot_sync(mask, cone_ok);
-        const float sa = sqrtf(fmaxf(fmaf(-kap, kap, 1.0f), 0.0f));
+        const float sa = sqrt_bound(fmaxf(fmaf(-kap, kap, 1.0f), 0.0f));
         // cos(beta + alpha), beta the angle between this lane's axis and aw, less a
         // margin; the distance from p0 to this lane's apex
         float kw = 1.0f, dw = 0.0f;
         if (cone_ok) {
             const float cb = fminf(dot(ax, aw), 1.0f);
-            const float sb = sqrtf(fmaxf(fmaf(-cb, cb, 1.0f), 0.0f));
+            const float sb = sqrt_bound(fmaxf(fmaf(-cb, cb, 1.0f), 0.0f));
             kw = fmaf(cb, kap, -sb * sa) - 0x1p-17f;
             kw = kw >= 0.5f ? kw : 0.0f;  // NaN: 0
             const f3 dp = sub(po, p0);
-            dw = sqrtf(dot(dp, dp));
+            dw = sqrt_bound(dot(dp, dp));
         }
         // warp minimum / maximum (non-negative floats order as their bits)
         const float kwm = __uint_as_float(__reduce_min_sync(mask, __float_as_uint(kw)));
         const float dwm = __uint_as_float(__reduce_max_sync(mask, __float_as_uint(dw)));
         const bool coarse = kwm >= 0.5f && dwm <= 0x1p30f;
-        const float rho = sqrtf(sc.cone_r2);
+        const float rho = sqrt_bound(sc.cone_r2);
         const float rw = (rho + dwm) * (1.0f + 0x1p-15f);
-        const float sw = sqrtf(fmaxf(fmaf(-kwm, kwm, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
+        const float sw = sqrt_bound(fmaxf(fmaf(-kwm, kwm, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
         const float sg = sa * (1.0f + 0x1p-18f);  // >= sin alpha
         own = cone_pass(sc.geo, h.ns_pad, mask, po, ax, fmaf(kap, kap, -0x1p-16f), 2.0f * rho * sg, sc.cone_r2,
                         cone_ok, cw, p0, aw, fmaf(kwm, kwm, -0x1p-16f), 2.0f * rw * sw, rw * rw * (1.0f + 0x1p-15f),
@@ -1235,7 +1235,7 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         const uint32_t* cone = cone_any && __all_sync(mask, pure) ? cw : nullptr;
         if (!cone && sc.cone_r2 > 0.0f && __all_sync(mask, allpt)) {
             const unsigned gu = __reduce_or_sync(mask, gl);
-            if (gu && point_pass(sc.geo, h.ns_pad, mask, h, p, p_lo, po, gl, gu, sqrtf(sc.cone_r2), cw + kConeWords))
+            if (gu && point_pass(sc.geo, h.ns_pad, mask, h, p, p_lo, po, gl, gu, sqrt_bound(sc.cone_r2), cw + kConeWords))
                 cone = cw + kConeWords;
         }
         static_assert(kFiltGroup == 4 && kConeGroup == 4, "one instance: every group has at most 4 segments");
@@ -1471,7 +1471,7 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
             // the blocks the warp's ray lines can reach (a view frustum for primary rays)
             if (sc.cone_r2 > 0.0f) {
                 uint32_t* cw = s_cone + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5) * 2 * kConeWords;
-                if (ray_cull(sc.geo, h.ns_pad, __activemask(), o, d, sqrtf(sc.cone_r2), sc.cone_cmax, cw)) cull = cw;
+                if (ray_cull(sc.geo, h.ns_pad, __activemask(), o, d, sqrt_bound(sc.cone_r2), sc.cone_cmax, cw)) cull = cw;
             }
         }
         const int id = closest_hit<CH, ACC>(sc, o, d, t, cull);
