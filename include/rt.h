@@ -260,27 +260,38 @@ rt_status rt_render_ws(const rt_scene *scene, const rt_camera *cam, const rt_ren
                        void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /* ---------------------------------------------------------------- batches
- * Many frames (scenes of uneven sphere counts and resolutions) rendered by ONE
- * persistent kernel launch: the (frame, tile) work items are ordered longest
- * first (estimated tile cost) and each CTA claims the next item with an atomic
- * add on a work counter until none is left, restaging the scene table in shared
- * memory when its frame changes.  Each pixel is computed exactly as rt_render
- * computes it (bit-identical output).  Not in the paper (which renders one frame
+ * Many frames (scenes of uneven sphere counts and resolutions) rendered by
+ * persistent kernels over a work queue: the (frame, tile) work items are ordered
+ * longest first (estimated tile cost) and each CTA claims the next item with an
+ * atomic add on a work counter until none is left, restaging the scene table in
+ * shared memory when its frame changes.  The items are split by shading path (the
+ * line filter from 128 spheres on, the segment test below), one persistent
+ * instance per class; the line-filter class's frames hand bounce-1 hits to bounce
+ * queues that one persistent pass per bounce works through (rt_render_ws's
+ * scheme).  Each pixel is computed exactly as rt_render computes it
+ * (bit-identical output).  Not in the paper (which renders one frame
  * per call, Section 3.9); it serves many small scenes at once.
  *   scenes[n], cams[n], params[n], outs_dev[n], pitches[n]: one entry per frame,
  *   with the same meaning and rules as for rt_render (hit records are not
  *   written).  Scenes must stay alive while the batch is in flight.  The batch
  *   kernel takes CTAs of at most 128 threads (block_x * block_y <= 128). */
 
-/* Device workspace bytes rt_render_batch needs (256-byte aligned buffer): a work
- * counter, the frame table and the item list.  0 on invalid arguments. */
+/* Device workspace bytes rt_render_batch needs (256-byte aligned buffer): the work
+ * counters, the frame table and the item list, then the bounce queues of the
+ * frames rendered with the line filter (scenes of 128 spheres or more) whose
+ * bounce limit is at least 1 -- a control block and two queues of a quarter of the
+ * frame's pixels, 64 bytes per entry (the queued render of rt_render_ws, inside the
+ * batch).  0 on invalid arguments. */
 size_t rt_batch_workspace_bytes(int32_t n, const rt_scene *const *scenes, const rt_render_params *params,
                                 const rt_launch_config *cfg);
 
 /* Enqueue one batched render on `stream` using the caller's workspace (no device
  * allocation): one host-to-device copy of the work tables (pageable source,
- * staged by the runtime before the call returns), then one kernel launch.  The
- * caller must not reuse the workspace before the launch completes. */
+ * staged by the runtime before the call returns), a reset of the bounce queues'
+ * counters, then the persistent kernels in stream order: the line-filter class's
+ * instance, one queue pass per bounce of its deferring frames, the segment-test
+ * class's instance (empty classes launch nothing).  The caller must not reuse the
+ * workspace before the launches complete. */
 rt_status rt_render_batch(int32_t n, const rt_scene *const *scenes, const rt_camera *cams,
                           const rt_render_params *params, void *const *outs_dev, const size_t *pitches,
                           void *workspace_dev, size_t workspace_bytes, const rt_launch_config *cfg,
@@ -290,7 +301,8 @@ typedef struct rt_batch rt_batch;   /* a planned batch captured in a CUDA graph 
 
 /* Plan a batch: validate, build the work tables, copy them to a library-owned
  * workspace (enqueued on `stream`), and capture a CUDA graph of {reset the work
- * counter, persistent kernel}.  Cameras and parameters are fixed at creation;
+ * counters and the bounce queues' counters, the persistent kernels and queue
+ * passes of rt_render_batch}.  Cameras and parameters are fixed at creation;
  * scene contents may change between launches (rt_scene_update). */
 rt_status rt_batch_create(int32_t n, const rt_scene *const *scenes, const rt_camera *cams,
                           const rt_render_params *params, void *const *outs_dev, const size_t *pitches,
@@ -312,9 +324,11 @@ rt_status rt_batch_free(rt_batch *batch);
  * list live in one fixed scratch array of RT_NOALLOC_SCRATCH_BYTES in the
  * library's device image (every GPU that loads the library holds it until the
  * process exits), filled by one host-to-device copy from a static host buffer.
- *   - At most RT_NOALLOC_MAX_FRAMES frames, and the work tables (see
- *     rt_batch_workspace_bytes) at most RT_NOALLOC_SCRATCH_BYTES: otherwise
- *     RT_ERR_EXCEEDS_SCRATCH and nothing is enqueued.
+ *   - At most RT_NOALLOC_MAX_FRAMES frames, and the work tables (work counters,
+ *     frame table, item list: rt_batch_workspace_bytes of a batch without bounce
+ *     queues) at most RT_NOALLOC_SCRATCH_BYTES: otherwise RT_ERR_EXCEEDS_SCRATCH
+ *     and nothing is enqueued.  No frame defers its bounces here (the queues would
+ *     not fit): the images are the same bits either way.
  *   - The first call on a device looks up the scratch array's device address
  *     (cudaGetSymbolAddress, with that device current).
  *   - It must not be captured into a CUDA graph: a captured copy would read the

@@ -626,9 +626,12 @@ rt_status ensure_smem(K kernel, size_t bytes) {
 
 // ------------------------------------------------------------ batch packing
 struct BatchPlanHost {
-    std::vector<unsigned char> table;  // workspace image: head, frames, items
+    std::vector<unsigned char> table;  // workspace image: head, frames, items, deferring frames
     int n_items = 0;
     int n_filt = 0;  // the first n_filt items: frames rendered with the line filter
+    int n_defer = 0, dmax = 0;  // frames with bounce queues, their largest bounce limit
+    size_t ctl_off = 0, ctl_bytes = 0;  // their control blocks (reset before every launch)
+    size_t ws_bytes = 0;                // the whole workspace (the queues follow the table)
     size_t smem = 0;
     bool chunked = false;
 };
@@ -637,6 +640,45 @@ struct BatchPlanHost {
 // passes) from kFilterMinPad spheres on, as rt_render does, unless the batch stages
 // its tables chunk by chunk.
 bool batch_filtered(const rt_scene* s, bool chunked) { return !chunked && s->ns_pad >= kFilterMinPad; }
+
+// The batch's bounce queues (rt_render_ws's scheme inside the batch): every frame of
+// the line-filter class with a bounce limit of at least 1 defers its bounce-1 paths,
+// with a quarter of its pixels per queue (a full queue is not an error: the lane
+// finishes the path itself).  Layout after the items (ending at items_end): the
+// deferring frames' indices (int), then their 256-byte control blocks, then each
+// frame's two queues.  Fills the frames' queue fields when `frames` is given and
+// returns the workspace's total size.
+size_t batch_defer_layout(int n, const rt_scene* const* scenes, const rt_render_params* params, bool chunked,
+                          size_t items_end, BatchFrame* frames, std::vector<int>* list, int* n_defer, int* dmax,
+                          size_t* ctl_off, size_t* ctl_bytes) {
+    int nd = 0, dm = 0;
+    for (int i = 0; i < n; ++i)
+        if (batch_filtered(scenes[i], chunked) && params[i].max_depth >= 1) {
+            ++nd;
+            dm = std::max(dm, params[i].max_depth);
+        }
+    const size_t c0 = (items_end + (size_t)nd * sizeof(int) + 255) / 256 * 256;
+    size_t off = c0 + (size_t)nd * kBatchQCtl;
+    int j = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!(batch_filtered(scenes[i], chunked) && params[i].max_depth >= 1)) continue;
+        const unsigned cap = (unsigned)std::min<size_t>(((size_t)params[i].width * params[i].height + 3) / 4,
+                                                        (size_t)1 << 30);
+        if (frames) {
+            frames[i].q_ctl = c0 + (size_t)j * kBatchQCtl;
+            frames[i].q_ent = off;
+            frames[i].q_cap = cap;
+        }
+        if (list) list->push_back(i);
+        off += 2 * (size_t)cap * kWsEntryBytes;
+        ++j;
+    }
+    *n_defer = nd;
+    *dmax = dm;
+    *ctl_off = c0;
+    *ctl_bytes = (size_t)nd * kBatchQCtl;
+    return nd ? off : items_end;  // no deferring frame: the work tables alone
+}
 
 // Relative cost of one tile of a frame, for the longest-first item order.
 double tile_cost(const rt_scene* s, const rt_render_params* p) {
@@ -696,8 +738,13 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
     for (int i = 0; i < n; ++i)
         if (batch_filtered(scenes[i], chunked)) n_filt += tiles[(size_t)i];
     const size_t items_off = batch_items_offset(n);
-    plan->table.assign(items_off + (size_t)n_items * 4, 0);
+    const size_t items_end = items_off + (size_t)n_items * 4;
+    std::vector<int> defer;
+    plan->ws_bytes = batch_defer_layout(n, scenes, params, chunked, items_end, frames.data(), &defer, &plan->n_defer,
+                                        &plan->dmax, &plan->ctl_off, &plan->ctl_bytes);
+    plan->table.assign(items_end + defer.size() * sizeof(int), 0);
     std::memcpy(plan->table.data() + batch_frames_offset(), frames.data(), (size_t)n * sizeof(BatchFrame));
+    if (!defer.empty()) std::memcpy(plan->table.data() + items_end, defer.data(), defer.size() * sizeof(int));
     uint32_t* items = reinterpret_cast<uint32_t*>(plan->table.data() + items_off);
     size_t k = 0;
     for (int f : order)
@@ -709,17 +756,19 @@ rt_status batch_pack(int n, const rt_scene* const* scenes, const rt_camera* cams
     return RT_OK;
 }
 
-// Resident CTAs of the batch kernel instances: grid[0] for the segment-test
-// instance, grid[1] for the line-filter one.
-rt_status batch_grid(const Launch& L, size_t smem, bool chunked, int grid[2]) {
+// Resident CTAs of the batch kernels: grid[0] for the segment-test instance,
+// grid[1] for the line-filter one, grid[2] for the queue passes.
+rt_status batch_grid(const Launch& L, size_t smem, bool chunked, int grid[3]) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
-    for (int fm = 0; fm < 2; ++fm) {
+    for (int fm = 0; fm < 3; ++fm) {
         int per_sm = 0;
         if (L.min_blocks > 0) {
             per_sm = L.min_blocks;
+        } else if (fm == 2) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_queue_kernel<1>, L.bx * L.by, smem);
         } else if (chunked) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_batch_kernel<true, 0>, L.bx * L.by, smem);
         } else {
@@ -737,18 +786,26 @@ rt_status batch_grid(const Launch& L, size_t smem, bool chunked, int grid[2]) {
 rt_status batch_smem(bool chunked, size_t smem) {
     if (chunked) return ensure_smem(rt_batch_kernel<true, 0>, smem);
     rt_status st = ensure_smem(rt_batch_kernel<false, 0>, smem);
-    return st != RT_OK ? st : ensure_smem(rt_batch_kernel<false, 1>, smem);
+    if (st == RT_OK) st = ensure_smem(rt_batch_kernel<false, 1>, smem);
+    return st != RT_OK ? st : ensure_smem(rt_batch_queue_kernel<1>, smem);
 }
 
-// The line-filter instance over items [0, n_filt), then the segment-test instance
-// over [n_filt, n_items), in stream order; an empty class launches nothing.
-void batch_launch(bool chunked, const int grid[2], const Launch& L, size_t smem, cudaStream_t st, unsigned char* ws,
-                  int n, int n_items, int n_filt) {
+// The line-filter instance over items [0, n_filt), the queue passes k = 1..dmax of
+// its deferring frames, then the segment-test instance over [n_filt, n_items), in
+// stream order; an empty class launches nothing.  Returns the number of launches.
+int batch_launch(bool chunked, const int grid[3], const Launch& L, size_t smem, cudaStream_t st, unsigned char* ws,
+                 int n, int n_items, int n_filt, int n_defer, int dmax) {
     const dim3 block(32, (L.bx * L.by) / 32);
     const int hstage = L.staging == 2 ? 2 : 1;
-    if (n_filt > 0)
+    int launches = 0;
+    if (n_filt > 0) {
         rt_batch_kernel<false, 1><<<grid[1], block, smem, st>>>(ws, n, 0, n_filt, hstage, L.bx, L.by);
+        ++launches;
+        for (int k = 1; n_defer > 0 && k <= dmax; ++k, ++launches)
+            rt_batch_queue_kernel<1><<<grid[2], block, smem, st>>>(ws, n, n_items, n_defer, k, hstage);
+    }
     if (n_items > n_filt) {
+        ++launches;
         if (chunked)
             rt_batch_kernel<true, 0><<<grid[0], block, smem, st>>>(ws, n, n_filt, n_items - n_filt, hstage, L.bx,
                                                                    L.by);
@@ -756,12 +813,14 @@ void batch_launch(bool chunked, const int grid[2], const Launch& L, size_t smem,
             rt_batch_kernel<false, 0><<<grid[0], block, smem, st>>>(ws, n, n_filt, n_items - n_filt, hstage, L.bx,
                                                                     L.by);
     }
+    return launches;
 }
 
 struct rt_batch {
     bool chunked = false;
-    int n = 0, n_items = 0, n_filt = 0;
-    int grid[2] = {0, 0};
+    int n = 0, n_items = 0, n_filt = 0, n_defer = 0, dmax = 0, launches = 0;
+    size_t table_bytes = 0, ctl_off = 0, ctl_bytes = 0;
+    int grid[3] = {0, 0, 0};
     Launch L{};
     size_t smem = 0, ws_bytes = 0;
     void* ws = nullptr;
@@ -1165,12 +1224,17 @@ size_t rt_batch_workspace_bytes(int32_t n, const rt_scene* const* scenes, const 
     Launch L;
     if (n < 1 || !scenes || !params || resolve_launch(cfg, &L) != RT_OK) return 0;
     size_t items = 0;
+    int max_pad = 0;
     for (int i = 0; i < n; ++i) {
         const rt_render_params* p = &params[i];
-        if (p->width < 1 || p->height < 1) return 0;
+        if (p->width < 1 || p->height < 1 || !scenes[i]) return 0;
         items += (size_t)((p->width + L.bx - 1) / L.bx) * (size_t)((p->height + L.by - 1) / L.by);
+        max_pad = std::max(max_pad, scenes[i]->ns_pad);
     }
-    return batch_items_offset(n) + items * 4;
+    int nd = 0, dm = 0;
+    size_t co = 0, cb = 0;
+    return batch_defer_layout(n, scenes, params, use_tiled_loop(L, max_pad), batch_items_offset(n) + items * 4, nullptr,
+                              nullptr, &nd, &dm, &co, &cb);
 }
 
 rt_status rt_render_batch(int32_t n, const rt_scene* const* scenes, const rt_camera* cams,
@@ -1181,18 +1245,19 @@ rt_status rt_render_batch(int32_t n, const rt_scene* const* scenes, const rt_cam
     if (st != RT_OK) return st;
     BatchPlanHost plan;
     if ((st = batch_pack(n, scenes, cams, params, outs_dev, pitches, L, &plan)) != RT_OK) return st;
-    if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) || workspace_bytes < plan.table.size())
+    if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) || workspace_bytes < plan.ws_bytes)
         return RT_ERR_INVALID_ARG;
     if ((st = batch_smem(plan.chunked, plan.smem)) != RT_OK) return st;
-    int grid[2] = {0, 0};
+    int grid[3] = {0, 0, 0};
     if ((st = batch_grid(L, plan.smem, plan.chunked, grid)) != RT_OK) return st;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     // pageable source: the runtime stages it before returning, so the vector may go
     cudaError_t e = cudaMemcpyAsync(workspace_dev, plan.table.data(), plan.table.size(), cudaMemcpyHostToDevice, st_);
+    if (e == cudaSuccess && plan.ctl_bytes)
+        e = cudaMemsetAsync(static_cast<unsigned char*>(workspace_dev) + plan.ctl_off, 0, plan.ctl_bytes, st_);
     if (e != cudaSuccess) return cuda_status(e);
-    batch_launch(plan.chunked, grid, L, plan.smem, st_, static_cast<unsigned char*>(workspace_dev), n, plan.n_items,
-                 plan.n_filt);
-    g_launches += (plan.n_filt > 0) + (plan.n_items > plan.n_filt);
+    g_launches += batch_launch(plan.chunked, grid, L, plan.smem, st_, static_cast<unsigned char*>(workspace_dev), n,
+                               plan.n_items, plan.n_filt, plan.n_defer, plan.dmax);
     return cuda_status(cudaGetLastError());
 }
 
@@ -1226,29 +1291,36 @@ rt_status rt_batch_create(int32_t n, const rt_scene* const* scenes, const rt_cam
     b->n = n;
     b->n_items = plan.n_items;
     b->n_filt = plan.n_filt;
+    b->n_defer = plan.n_defer;
+    b->dmax = plan.dmax;
+    b->ctl_off = plan.ctl_off;
+    b->ctl_bytes = plan.ctl_bytes;
     b->L = L;
     b->smem = plan.smem;
-    b->ws_bytes = plan.table.size();
+    b->ws_bytes = plan.ws_bytes;
+    b->table_bytes = plan.table.size();
     if ((st = batch_grid(L, plan.smem, plan.chunked, b->grid)) != RT_OK) {
         rt_batch_free(b);
         return st;
     }
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMalloc(&b->ws, b->ws_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->pinned, b->ws_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->pinned, b->table_bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
-        std::memcpy(b->pinned, plan.table.data(), b->ws_bytes);
-        e = cudaMemcpyAsync(b->ws, b->pinned, b->ws_bytes, cudaMemcpyHostToDevice, st_);
+        std::memcpy(b->pinned, plan.table.data(), b->table_bytes);
+        e = cudaMemcpyAsync(b->ws, b->pinned, b->table_bytes, cudaMemcpyHostToDevice, st_);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->ready, st_);
-    // graph: reset the two work counters, then the persistent kernel instances
+    // graph: reset the two work counters and the bounce queues' counters, then the
+    // persistent kernel instances and the queue passes
     if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(b->ws, 0, 2 * sizeof(unsigned), b->cap);
-        batch_launch(b->chunked, b->grid, L, b->smem, b->cap, static_cast<unsigned char*>(b->ws), n, b->n_items,
-                     b->n_filt);
+        if (b->ctl_bytes) cudaMemsetAsync(static_cast<unsigned char*>(b->ws) + b->ctl_off, 0, b->ctl_bytes, b->cap);
+        b->launches = batch_launch(b->chunked, b->grid, L, b->smem, b->cap, static_cast<unsigned char*>(b->ws), n,
+                                   b->n_items, b->n_filt, b->n_defer, b->dmax);
         cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = e2;
@@ -1267,7 +1339,7 @@ rt_status rt_batch_launch(rt_batch* b, void* stream) {
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamWaitEvent(st_, b->ready, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st_);
-    if (e == cudaSuccess) g_launches += (b->n_filt > 0) + (b->n_items > b->n_filt);
+    if (e == cudaSuccess) g_launches += b->launches;
     return cuda_status(e);
 }
 
@@ -1479,14 +1551,14 @@ extern "C" rt_status rt_render_batch_noalloc(int32_t n, const rt_scene* const* s
                           &bytes, &n_items, &n_filt, &smem, &chunked);
     if (st != RT_OK) return st;
     if ((st = batch_smem(chunked, smem)) != RT_OK) return st;
-    int grid[2] = {0, 0};
+    int grid[3] = {0, 0, 0};
     if ((st = batch_grid(L, smem, chunked, grid)) != RT_OK) return st;
     // pageable source: staged by the runtime before the call returns, so the static
     // host image is free for the next call
     e = cudaMemcpyAsync(g_noalloc_dev_ptr[dev], g_noalloc_host, bytes, cudaMemcpyHostToDevice, st_);
     if (e != cudaSuccess) return cuda_status(e);
-    batch_launch(chunked, grid, L, smem, st_, static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]), n, n_items,
-                 n_filt);
-    g_launches += (n_filt > 0) + (n_items > n_filt);
+    // no bounce queues: the scratch holds the work tables only
+    g_launches += batch_launch(chunked, grid, L, smem, st_, static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]), n,
+                               n_items, n_filt, 0, 0);
     return cuda_status(cudaGetLastError());
 }

@@ -20,7 +20,7 @@ the 4K workload measures 2.8e-4 in F32).
 RGBA8: within 1 LSB per channel for >= 99.99% of pixels, and any pixel beyond
 1 LSB must be margin- or sensitivity-exempt.
 
-The sensitivity costs four more oracle traces per pixel, so it is computed only
+The sensitivity costs forty more oracle traces per pixel, so it is computed only
 for the pixels that need it (those beyond the plain tolerance and not
 margin-exempt).
 """

@@ -66,3 +66,32 @@ def test_small_batch_matches_oracle():
         ref, margin, sens = oracle_reference(w)
         ok, st = compare_f32(o.cpu().numpy()[..., :3].reshape(-1, 3), ref, margin, sens, w.scene.scene_scale)
         assert st["failing"] == 0 and st["frac_within_1e-4"] >= 0.98, (w.name, st)
+
+
+def test_bounce_queues_rgba8_and_deep_mirrors():
+    """Frames of the line-filter class with bounce limits 1..16 defer their
+    bounce-1 paths to the batch's bounce queues; RGBA8 frames (four lanes share a
+    store, a deferred pixel is overwritten by the pass that finishes it) and a
+    scene of mirror spheres whose paths run to bounce 16 equal rt_render bit for
+    bit, and so do the frames of the segment-test class in the same batch."""
+    ws = S.batch_scenes(10, seed0=800)
+    sc = S.random_scene(901, 160, 2, 3.0)
+    sc.spheres = sc.spheres.copy()
+    sc.spheres[:, 9] = np.float32(0.9)                  # mirrors: long reflection chains
+    ws.append(S.Workload("mirrors_d16", sc, S.default_camera(3.0),
+                         S._params(sc, width=200, height=120, max_depth=16, seed=901)))
+    for i, w in enumerate(ws):
+        if i % 2 == 0:
+            w.params.out_format = S.OUT_RGBA8
+    assert any(w.scene.n_spheres >= 121 and w.params.max_depth >= 1 for w in ws)
+    dss = [rt.DeviceScene(w.scene) for w in ws]
+    ref = per_frame(ws, dss)
+    outs, _ = rt.render_batch(dss, [w.camera for w in ws], [w.params for w in ws])
+    b = rt.Batch(dss, [w.camera for w in ws], [w.params for w in ws])
+    b.launch()
+    torch.cuda.synchronize()
+    for i, (a, o, g) in enumerate(zip(ref, outs, b.outputs())):
+        assert np.array_equal(a, o.cpu().numpy()), (i, ws[i].name)
+        assert np.array_equal(a, g.cpu().numpy()), (i, ws[i].name)
+    assert rt.device_errors() == 0
+    b.close()
