@@ -578,9 +578,13 @@ def bvh_extra(dev, stream):
     import torch
     from paper_2305_07450_b300 import autotune, rt
     big = S.random_scene(41, 4096, 2, 12.0, area_lights=1)
+    huge = S.random_scene(43, 8192, 2, 16.0, area_lights=1)
     cases = [workload("4k"), workload("4k_scene_1080p"),
              S.Workload("1920x1080_4096sph_2pt+area16_d4_rgba8", big, S.default_camera(12.0),
-                        S._params(big, width=1920, height=1080, max_depth=4, shadow_samples=16, seed=41))]
+                        S._params(big, width=1920, height=1080, max_depth=4, shadow_samples=16, seed=41)),
+             # beyond the brute force's cone pre-pass (tables of at most 4096 spheres)
+             S.Workload("1280x720_8192sph_2pt+area16_d4_rgba8", huge, S.default_camera(16.0),
+                        S._params(huge, width=1280, height=720, max_depth=4, shadow_samples=16, seed=43))]
     res = {}
     for w in cases:
         ds = rt.DeviceScene(w.scene)
