@@ -31,6 +31,9 @@ static std::atomic<uint64_t> g_launches{0};
 struct rt_scene {
     int ns = 0, ns_pad = 0, has_plane = 0, nl = 0;
     int any_area = 0, any_sphere_light = 0;
+    // the light kinds above describe the device contents (false after a device-side
+    // update, which may change them; the lean kernels are then not chosen)
+    bool kinds_known = true;
     size_t bytes = 0;
     void* dev = nullptr;     // device blob: header, geo, mat, mat2
     void* pinned = nullptr;  // host staging of the blob
@@ -45,10 +48,22 @@ struct rt_scene {
     size_t bvh_cap = 0;
     cudaEvent_t bvh_copy_done = nullptr;
     rt_bvh_info bvh_info{};
+
     // sky panorama (Section 3.8): sky_h rows of sky_w RGBA texels, or none
     void* sky_dev = nullptr;
     int sky_w = 0, sky_h = 0;
 };
+
+// Which kinds of light a host description holds (area squares, spherical lights).
+static void set_light_kinds(rt_scene* s, const rt_scene_desc* desc) {
+    s->any_area = 0;
+    s->any_sphere_light = 0;
+    for (int l = 0; l < desc->n_lights; ++l) {
+        if (desc->lights[8 * l + 4] > 0.f) s->any_area = 1;
+        if (desc->lights[8 * l + 5] > 0.f) s->any_sphere_light = 1;
+    }
+    s->kinds_known = true;
+}
 
 static SceneView view_of(const rt_scene* s) {
     const char* b = static_cast<const char*>(s->dev);
@@ -71,7 +86,7 @@ static SceneView view_of(const rt_scene* s) {
 // 9.97 ms against 10.22 at 80, 10.11 at 96, 10.48 at 104, 10.25 at 112, 10.46 at
 // 144, 10.39 at 168; with groups of 7 the one-pass kernel too: 11.73 ms at 128
 // against 12.05 ms for groups of 4 at 80).
-constexpr int fwd_regs(int fm) { return fm == 1 ? 128 : 80; }
+constexpr int fwd_regs(int fm) { return fm_path(fm) == 1 ? 128 : 80; }
 
 
 // One thread per pixel.  The CTA covers block_x x block_y pixels; warp w covers an
@@ -101,7 +116,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_kernel(const SceneView sv, cons
     StagedScene sc{hdr, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)warp * kChunk : nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (FM == 1 && !CH) staged_cone(tab, hdr->ns_pad, sc);
+    if constexpr (fm_path(FM) == 1 && !CH) staged_cone(tab, hdr->ns_pad, sc);
 
     const int wpr = block_x >> 3;
     const int x = fr.rx0 + blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
@@ -157,7 +172,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_p0_kernel(const SceneView sv, c
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (FM == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
+    if constexpr (fm_path(FM) == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
     WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
     const PathQueue q1 = ws_queue(ws, cap, 1);
     const int wpr = block_x >> 3, wpt = (block_x * block_y) >> 5;
@@ -191,7 +206,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv
     __shared__ uint64_t bar;
     WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
     const unsigned n = min(*reinterpret_cast<volatile unsigned*>(&ctl->count[k]), cap);
-    const bool wide = FM == 1 && n <= wide_max;
+    const bool wide = fm_path(FM) == 1 && n <= wide_max;
     const unsigned per_cta = wide ? blockDim.y : 32u * blockDim.y;
     if ((unsigned)blockIdx.x * per_cta >= n) return;  // the whole CTA, before any barrier
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -205,10 +220,10 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (FM == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
+    if constexpr (fm_path(FM) == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
     const PathQueue cur = ws_queue(ws, cap, k);
     const PathQueue nxt = ws_queue(ws, cap, k + 1);
-    if constexpr (FM == 1) {
+    if constexpr (fm_path(FM) == 1) {
         if (wide) {
 #pragma unroll 1
             while (true) {
@@ -216,7 +231,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv
                 if (lane == 0) i = atomicAdd(&ctl->head[k], 1u);
                 i = __shfl_sync(0xffffffffu, i, 0);
                 if (i >= n) break;
-                trace_queued_wide<HITREC>(sc, fr, cur.ent + (size_t)i * 4, k, out, pitch, hr, hr_plane);
+                trace_queued_wide<HITREC, fm_lean(FM)>(sc, fr, cur.ent + (size_t)i * 4, k, out, pitch, hr, hr_plane);
                 __syncwarp();
             }
             return;
@@ -942,10 +957,7 @@ rt_status rt_scene_upload(const rt_scene_desc* desc, void* stream, rt_scene** ou
     s->ns_pad = pad_spheres(desc->n_spheres);
     s->has_plane = desc->has_plane ? 1 : 0;
     s->nl = desc->n_lights;
-    for (int l = 0; l < desc->n_lights; ++l) {
-        if (desc->lights[8 * l + 4] > 0.f) s->any_area = 1;
-        if (desc->lights[8 * l + 5] > 0.f) s->any_sphere_light = 1;
-    }
+    set_light_kinds(s, desc);
     s->bytes = scene_bytes(s->ns_pad);
     cudaGetDevice(&s->device);
     cudaError_t e = cudaMalloc(&s->dev, s->bytes);
@@ -980,11 +992,13 @@ rt_status rt_scene_update(rt_scene* s, const rt_scene_desc* desc, int32_t desc_o
                                                          desc->plane, s->nl, desc->lights);
         g_launches++;
         s->host_current = false;
+        s->kinds_known = false;
         if (s->bvh_state) s->bvh_state = 2;
         return cuda_status(cudaGetLastError());
     }
     rt_status st = validate_desc(desc);
     if (st != RT_OK) return st;
+    set_light_kinds(s, desc);
     cudaError_t e = cudaEventSynchronize(s->copy_done);  // the previous copy has left the staging buffer
     if (e != cudaSuccess) return cuda_status(e);
     pack_host(desc, s->ns_pad, static_cast<unsigned char*>(s->pinned));
@@ -1126,6 +1140,8 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
     // the sunflower table of a spherical light's samples follows the staged data (from
     // 16 samples on: with fewer, its set-up per CTA costs more than it saves)
     const int flower_n = s->any_sphere_light && p->shadow_samples >= 16 ? p->shadow_samples : 0;
+    // no sky and, as far as the host knows, no spherical light: the lean kernels
+    const bool lean = !s->sky_dev && s->kinds_known && !s->any_sphere_light;
     const bool chunked = use_tiled_loop(L, s->ns_pad, (size_t)flower_n * 16);
     const uint32_t flower_off = (uint32_t)((stage_smem_bytes(chunked, s->ns_pad, nwarps) + 15) / 16 * 16);
     const size_t smem = flower_off + (size_t)flower_n * 16;
@@ -1160,10 +1176,12 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         }                                                                                                         \
     } while (0)
         if (hr) {
-            if (filt) RT_WS_LAUNCH(true, 1);
+            if (filt && lean) RT_WS_LAUNCH(true, 1 | kFmLean);
+            else if (filt) RT_WS_LAUNCH(true, 1);
             else RT_WS_LAUNCH(true, 0);
         } else {
-            if (filt) RT_WS_LAUNCH(false, 1);
+            if (filt && lean) RT_WS_LAUNCH(false, 1 | kFmLean);
+            else if (filt) RT_WS_LAUNCH(false, 1);
             else RT_WS_LAUNCH(false, 0);
         }
 #undef RT_WS_LAUNCH
@@ -1180,10 +1198,12 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
     const bool filt = !chunked && s->ns_pad >= kFilterMinPad;
     if (hr) {
         if (chunked) RT_FWD_LAUNCH(true, true, 0);
+        else if (filt && lean) RT_FWD_LAUNCH(true, false, 1 | kFmLean);
         else if (filt) RT_FWD_LAUNCH(true, false, 1);
         else RT_FWD_LAUNCH(true, false, 0);
     } else {
         if (chunked) RT_FWD_LAUNCH(false, true, 0);
+        else if (filt && lean) RT_FWD_LAUNCH(false, false, 1 | kFmLean);
         else if (filt) RT_FWD_LAUNCH(false, false, 1);
         else RT_FWD_LAUNCH(false, false, 0);
     }
