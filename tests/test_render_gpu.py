@@ -278,3 +278,48 @@ def test_maximum_frame_dimensions():
         ok, st = compare_f32(sub[..., :3].reshape(-1, 3), ref, margin, sens, w.scene.scene_scale)
         assert st["failing"] == 0, (x0, y0, st)
     ds.close()
+
+
+def test_lean_kernels_follow_the_light_kinds():
+    """The line-filter kernels built without the spherical-light sample code run only
+    while the host knows the scene has no spherical light.  A scene that gains one by
+    a host-side update, or by a device-side update (the light kinds are unknown from
+    then on), renders exactly as a fresh upload of it does, in one pass and queued,
+    and matches the oracle on a lattice of pixels."""
+    base = S.random_scene(11, 256, 3, 4.0)
+    p = S._params(base, width=160, height=96, max_depth=3, shadow_samples=16, out_format=S.OUT_F32, seed=11)
+    cam = S.default_camera(4.0)
+    lit = copy.deepcopy(base)
+    lit.lights[0, 5] = np.float32(1.5)  # light 0 becomes a sphere of radius 1.5
+    launches = (None, {"block_x": 8, "block_y": 32, "queued": 1, "staging": 1})
+
+    def frames(ds):
+        out = [rt.render(ds, cam, p, launch=L).cpu().numpy() for L in launches]
+        torch.cuda.synchronize()
+        assert rt.device_errors() == 0
+        return out
+
+    fresh = rt.DeviceScene(lit)
+    want = frames(fresh)
+    fresh.close()
+    assert np.array_equal(want[0], want[1])
+    plain = rt.DeviceScene(base)
+    before = frames(plain)
+    assert not np.array_equal(before[0], want[0])  # the light's change shows
+    plain.update(lit)
+    for a, b in zip(frames(plain), want):
+        assert np.array_equal(a, b)
+    plain.close()
+    dev = rt.DeviceScene(base)
+    frames(dev)
+    dev.update(spheres=torch.from_numpy(lit.spheres).cuda(), plane=torch.from_numpy(lit.plane).cuda(),
+               lights=torch.from_numpy(lit.lights).cuda())
+    for a, b in zip(frames(dev), want):
+        assert np.array_equal(a, b)
+    dev.close()
+    w = S.Workload("lean_light_kinds", lit, cam, p)
+    px = S.pixel_lattice(p.width, p.height, 7, seed=11, n_random=64)
+    ref, margin, sens = oracle_reference(w, px)
+    got = want[0][px[:, 1], px[:, 0], :3].reshape(-1, 3)
+    ok, st = compare_f32(got, ref, margin, sens, lit.scene_scale)
+    assert st["failing"] == 0, st
