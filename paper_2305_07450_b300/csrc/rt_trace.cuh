@@ -1159,19 +1159,42 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
         out.S = fmaf(iv * ks, sp, out.S);
         if (HITREC) hr[hr_k + (size_t)(2 + li) * hr_plane] = vis;
     };
-    // the skipped light's result, in light order: when the next light to attribute is it
-    auto flush_skipped = [&]() {
-        if (!skip_done && cl == lc) {
-            attribute(lc, 1.0f);
-            skip_done = true;
+    const float kv = kap + 0x1p-18f;
+    int kp = 0;       // results of the previous group not yet attributed
+    uint32_t bp = 0;  // their blocked bits
+#pragma unroll 1
+    while (true) {
+        // Attribute in light order: the previous group's results as each light's
+        // segments complete, and the skipped light (visibility 1) in its turn.  One
+        // call site, so that the shading code is compiled once into the group loop; the
+        // loop leaves only after this step, which then finds the last results.
+        int j = 0;
+#pragma unroll 1
+        while (true) {
+            float vis = 1.0f;
+            if (skip_done || cl != lc) {
+                bool ready = false;
+#pragma unroll 1
+                while (j < kp) {
+                    cnt += (bp >> j) & 1u ? 0 : 1;
+                    ++j;
+                    const int nr = rays_of_light(fr, h.light_s[cl]);
+                    if (++cs == nr) {
+                        vis = (float)cnt / (float)nr;
+                        cs = 0;
+                        cnt = 0;
+                        ready = true;
+                        break;
+                    }
+                }
+                if (!ready) break;
+            } else {
+                skip_done = true;
+            }
+            attribute(cl, vis);
             const uint32_t rest = lit & ~((2u << cl) - 1u);
             cl = rest ? __ffs(rest) - 1 : 0;
         }
-    };
-    flush_skipped();
-    const float kv = kap + 0x1p-18f;
-#pragma unroll 1
-    while (true) {
         // a group ends before the cone light's first segment, so that its segments
         // form groups of their own (of kConeGroup)
         const int lim = cone_ok && done < before_lc ? before_lc : total;
@@ -1241,25 +1264,11 @@ __device__ __forceinline__ HitShade shade_hit_staged(const StagedScene& sc, cons
                 cone = cw + kConeWords;
         }
         static_assert(kFiltGroup == 4 && kConeGroup == 4, "one instance: every group has at most 4 segments");
-        blocked = occluded_filtered<kFiltGroup, IT>(sc.geo, h.ns_pad, mask, po, blocked, seg, exact_only, cone, own,
-                                                items && cone == cw);
-        // attribute the results to their lights in the same order
-#pragma unroll 1
-        for (int j = 0; j < kr; ++j) {
-            cnt += (blocked >> j) & 1u ? 0 : 1;
-            const int nr = rays_of_light(fr, h.light_s[cl]);
-            if (++cs == nr) {
-                attribute(cl, (float)cnt / (float)nr);
-                cs = 0;
-                cnt = 0;
-                const uint32_t rest = lit & ~((2u << cl) - 1u);
-                cl = rest ? __ffs(rest) - 1 : 0;
-                flush_skipped();
-            }
-        }
+        bp = occluded_filtered<kFiltGroup, IT>(sc.geo, h.ns_pad, mask, po, blocked, seg, exact_only, cone, own,
+                                           items && cone == cw);
+        kp = kr;
         done += kr;
     }
-    flush_skipped();
     return out;
 }
 
