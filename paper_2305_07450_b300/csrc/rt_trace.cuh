@@ -109,9 +109,64 @@ __device__ __forceinline__ RayCross ray_cross(f3 o, f3 d) {
                     dup2(-d.z),   dup2(x.nw.x), dup2(x.nw.y), dup2(x.nw.z), x.nod};
 }
 
+// m of sphere hf of pair q: the packed operations of the pair, one half.
+__device__ __forceinline__ float sphere_m(const float4 A, const float4 B, int hf, const RayCross& r) {
+    const float cx = hf ? A.y : A.x, cy = hf ? A.w : A.z, cz = hf ? B.y : B.x, nr = hf ? B.w : B.z;
+    const float px = fmaf(cy, r.dz.x, fmaf(cz, r.ndy.x, r.nwx.x));
+    const float py = fmaf(cz, r.dx.x, fmaf(cx, r.ndz.x, r.nwy.x));
+    const float pz = fmaf(cx, r.dy.x, fmaf(cy, r.ndx.x, r.nwz.x));
+    return fmaf(px, px, fmaf(py, py, fmaf(pz, pz, nr)));
+}
+// closest_block with the roots of the flagged spheres in one copy of the code.
+__device__ __forceinline__ void closest_block_compact(const float4* __restrict__ geo, int base, const RayCross& r,
+                                                      float& tb, int& best) {
+    uint32_t neg = 0;  // bit i: sphere i's m has its sign bit set
+#pragma unroll
+    for (int q = 0; q < kPad / 2; ++q) {
+        const float4 A = geo[2 * q], B = geo[2 * q + 1];
+        const float2 cx = make_float2(A.x, A.y), cy = make_float2(A.z, A.w), cz = make_float2(B.x, B.y);
+        const float2 px = fma2(cy, r.dz, fma2(cz, r.ndy, r.nwx));
+        const float2 py = fma2(cz, r.dx, fma2(cx, r.ndz, r.nwy));
+        const float2 pz = fma2(cx, r.dy, fma2(cy, r.ndx, r.nwz));
+        const float2 m = fma2(px, px, fma2(py, py, fma2(pz, pz, make_float2(B.z, B.w))));
+        neg |= ((__float_as_uint(m.x) >> 31) | ((__float_as_uint(m.y) >> 31) << 1)) << (2 * q);
+    }
+    // the roots of the flagged spheres in index order, one copy of the code: m is
+    // formed again by the same operations (a fused multiply-add per lane, so the
+    // scalar form gives the packed one's bits)
+#pragma unroll 1
+    while (neg) {
+        const int i = __ffs(neg) - 1;
+        neg &= neg - 1u;
+        const float4 A = geo[2 * (i >> 1)], B = geo[2 * (i >> 1) + 1];
+        const int hf = i & 1;
+        const float mm = sphere_m(A, B, hf, r);
+        if (mm < 0.0f) {
+            const float cx = hf ? A.y : A.x, cy = hf ? A.w : A.z, cz = hf ? B.y : B.x;
+            const float tc = fmaf(cx, r.dx.x, fmaf(cy, r.dy.x, fmaf(cz, r.dz.x, r.nod)));
+            const float s = __fsqrt_rn(-mm);
+            float t = tc - s;
+            if (t <= 0.0f) t = tc + s;
+            if (t > 0.0f && t < tb) {
+                tb = t;
+                best = base + i;
+            }
+        }
+    }
+}
+
 // One block of kPad spheres (kPad / 2 pairs at geo[0..kPad)); base = index of its first sphere.
+// COMPACT: the roots of the flagged spheres through one copy of the code (the
+// line-filter kernels, whose code outgrows the instruction cache: 4K frame 3.80 ->
+// 3.61 ms); otherwise unrolled per sphere (the segment-test kernels: 1080p 0.272 ->
+// 0.267 ms against the compact form).  Both give the same bits.
+template <bool COMPACT>
 __device__ __forceinline__ void closest_block(const float4* __restrict__ geo, int base, const RayCross& r, float& tb,
                                               int& best) {
+    if constexpr (COMPACT) {
+        closest_block_compact(geo, base, r, tb, best);
+        return;
+    }
     float2 m[kPad / 2];
     uint32_t neg = 0;
 #pragma unroll
@@ -149,7 +204,7 @@ __device__ __forceinline__ void closest_block(const float4* __restrict__ geo, in
 
 // blocks: the blocks of kPad spheres to test (bits, ray_cull), or null: every
 // block (the staged table only; visited in index order either way).
-template <bool CH, bool ACC = false>
+template <bool CH, bool ACC = false, bool COMPACT = false>
 __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, float& t_out,
                                            const uint32_t* blocks = nullptr) {
     float tb = __int_as_float(0x7f800000);  // +inf
@@ -166,7 +221,7 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
                 const int m = min(kChunk, n - c0);
                 stage_chunk(sc, mask, c0, m);
 #pragma unroll 1
-                for (int i0 = 0; i0 < m; i0 += kPad) closest_block(sc.chunk + i0, c0 + i0, rp, tb, best);
+                for (int i0 = 0; i0 < m; i0 += kPad) closest_block<COMPACT>(sc.chunk + i0, c0 + i0, rp, tb, best);
             }
         } else {
             const int nb = n / kPad;
@@ -177,7 +232,7 @@ __device__ __forceinline__ int closest_hit(const StagedScene& sc, f3 o, f3 d, fl
                 while (m) {
                     const int i0 = (w0 + __ffs(m) - 1) * kPad;
                     m &= m - 1u;
-                    closest_block(sc.geo + i0, i0, rp, tb, best);
+                    closest_block<COMPACT>(sc.geo + i0, i0, rp, tb, best);
                 }
             }
         }
@@ -1494,7 +1549,7 @@ __device__ __forceinline__ float3 trace_pixel(const StagedScene& sc, const Frame
                 if (ray_cull(sc.geo, h.ns_pad, __activemask(), o, d, sqrt_bound(sc.cone_r2), sc.cone_cmax, cw)) cull = cw;
             }
         }
-        const int id = closest_hit<CH, ACC>(sc, o, d, t, cull);
+        const int id = closest_hit<CH, ACC, fm_path(FM) == 1>(sc, o, d, t, cull);
         if (HITREC) {
             float* rec = hr + (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
             rec[0] = __int_as_float(id);
@@ -1612,7 +1667,7 @@ __device__ __forceinline__ void trace_queued(const StagedScene& sc, const Frame&
             break;
         }
         ++k;
-        id = closest_hit<false, false>(sc, o, d, t);
+        id = closest_hit<false, false, fm_path(FM) == 1>(sc, o, d, t);
         if (HITREC) {
             float* rec = hr + (size_t)k * (2 + h.nl) * hr_plane + hr_pix;
             rec[0] = __int_as_float(id);
@@ -1652,7 +1707,7 @@ __device__ __forceinline__ int closest_hit_wide(const StagedScene& sc, f3 o, f3 
     const int n = sc.hdr->ns_pad;
     const RayCross rp = ray_cross(o, d);
 #pragma unroll 1
-    for (int i0 = lane * kPad; i0 < n; i0 += 32 * kPad) closest_block(sc.geo + i0, i0, rp, tb, best);
+    for (int i0 = lane * kPad; i0 < n; i0 += 32 * kPad) closest_block<true>(sc.geo + i0, i0, rp, tb, best);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const float t2 = __shfl_xor_sync(0xffffffffu, tb, off);
