@@ -447,6 +447,20 @@ __device__ __forceinline__ bool cone_block_clear(const float4* __restrict__ g, c
     return (clr >> 31) != 0;
 }
 
+// The blocks of the table split over the lanes (this lane's share: rank, rank +
+// cnt, ...), each tested once against one cone (apex, unit axis, c0 = kappa^2 -
+// 2^-16, tw = 2 rho sigma, r2 = rho^2 with its slack); bit b of cw is set for every
+// block the cone does not clear.  One copy of the loop for every warp-cone pass.
+__device__ __noinline__ void cone_blocks_split(const float4* __restrict__ geo, int nb, int rank, int cnt, f3 apex,
+                                               f3 axis, float c0, float tw, float r2, uint32_t* cw) {
+    const RayPair o2 = ray_pair(apex);
+    const float2 ax = dup2(axis.x), ay = dup2(axis.y), az = dup2(axis.z);
+    const float2 nc0 = dup2(-c0), tw2 = dup2(tw), r22 = dup2(r2);
+#pragma unroll 1
+    for (int b = rank; b < nb; b += cnt)
+        if (!cone_block_clear(geo + (size_t)b * kPad, o2, ax, ay, az, nc0, tw2, r22)) atomicOr(&cw[b >> 5], 1u << (b & 31));
+}
+
 // The warp's block bits for the cones of the lanes in `mask` whose `use` is set (this
 // lane's cone: apex o, axis ax, c0, twors, rho2), written to cw[0 .. n / kPad / 32].
 // With `coarse`, a first pass splits the blocks over the lanes and tests each once
@@ -466,13 +480,7 @@ __device__ __noinline__ uint32_t cone_pass(const float4* __restrict__ geo, int n
         const int rank = __popc(mask & ((1u << lane) - 1u)), cnt = __popc(mask);
         for (int w = rank; w < (nb + 31) / 32; w += cnt) cw[w] = 0u;
         __syncwarp(mask);
-        const RayPair q2 = ray_pair(p0);
-        const float2 bx = dup2(aw.x), by = dup2(aw.y), bz = dup2(aw.z);
-        const float2 bc0 = dup2(-wc0), btw = dup2(wtw), br2 = dup2(wr2);
-#pragma unroll 1
-        for (int b = rank; b < nb; b += cnt)
-            if (!cone_block_clear(geo + (size_t)b * kPad, q2, bx, by, bz, bc0, btw, br2))
-                atomicOr(&cw[b >> 5], 1u << (b & 31));
+        cone_blocks_split(geo, nb, rank, cnt, p0, aw, wc0, wtw, wr2, cw);
         __syncwarp(mask);
     }
     const RayPair o2 = ray_pair(o);
@@ -536,13 +544,8 @@ __device__ __noinline__ bool ray_cull(const float4* __restrict__ geo, int n, uns
     const int rank = __popc(mask & ((1u << lane) - 1u)), cnt = __popc(mask);
     for (int w = rank; w < (nb + 31) / 32; w += cnt) cw[w] = 0u;
     __syncwarp(mask);
-    const RayPair o2 = ray_pair(p0);
-    const float2 ax = dup2(a.x), ay = dup2(a.y), az = dup2(a.z);
-    const float2 c0 = dup2(-fmaf(kw, kw, -0x1p-16f)), tw = dup2(2.0f * rho * sw);
-    const float2 r2 = dup2(rho * rho * (1.0f + 0x1p-15f));
-#pragma unroll 1
-    for (int b = rank; b < nb; b += cnt)
-        if (!cone_block_clear(geo + (size_t)b * kPad, o2, ax, ay, az, c0, tw, r2)) atomicOr(&cw[b >> 5], 1u << (b & 31));
+    cone_blocks_split(geo, nb, rank, cnt, p0, a, fmaf(kw, kw, -0x1p-16f), 2.0f * rho * sw,
+                      rho * rho * (1.0f + 0x1p-15f), cw);
     __syncwarp(mask);
     return true;
 }
@@ -594,14 +597,8 @@ __device__ __noinline__ bool point_pass(const float4* __restrict__ geo, int n, u
             break;
         }
         const float sw = sqrt_bound(fmaxf(fmaf(-kw, kw, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);
-        const RayPair o2 = ray_pair(L);
-        const float2 ax = dup2(a.x), ay = dup2(a.y), az = dup2(a.z);
-        const float2 c0 = dup2(-fmaf(kw, kw, -0x1p-16f)), tw = dup2(2.0f * rl * sw);
-        const float2 r2 = dup2(rl * rl * (1.0f + 0x1p-15f));
-#pragma unroll 1
-        for (int b = rank; b < nb; b += cnt)
-            if (!cone_block_clear(geo + (size_t)b * kPad, o2, ax, ay, az, c0, tw, r2))
-                atomicOr(&cw[b >> 5], 1u << (b & 31));
+        cone_blocks_split(geo, nb, rank, cnt, L, a, fmaf(kw, kw, -0x1p-16f), 2.0f * rl * sw,
+                          rl * rl * (1.0f + 0x1p-15f), cw);
     }
     __syncwarp(mask);
     return ok;
@@ -632,36 +629,40 @@ __device__ __forceinline__ void pair_exact(const float4* __restrict__ geo, int q
 }
 
 // One block of kPad spheres through the filter; the segment test for the pairs
-// some lane flags.  Returns true when every segment of every lane in `mask` is
-// blocked (checked only after a segment test ran: the filter alone blocks nothing).
+// some lane flags (every pair with `force`, warp-uniform: the filter skipped).
+// Returns true when every segment of every lane in `mask` is blocked (checked only
+// after a segment test ran: the filter alone blocks nothing).
 template <int R>
 __device__ __forceinline__ bool occluded_block_filtered(const float4* __restrict__ geo, unsigned mask,
                                                         const RayPair& o2, const SegFilt (&sf)[kFiltGroup],
-                                                        const float* seg, uint32_t (&acc)[kFiltGroup]) {
-    uint32_t clear[kPad / 2];
-#pragma unroll
-    for (int q = 0; q < kPad / 2; ++q) {
-        const float4 A = geo[2 * q], B = geo[2 * q + 1];
-        const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
-        const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
-        const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
-        const float2 oc2 = fma2(ocx, ocx, fma2(ocy, ocy, mul2(ocz, ocz)));
-        // K2 r^2 - K1 |oc|^2 (B.zw = -r^2), and |oc|^2 - 2^100 (positive: too large)
-        const float2 c = fma2(oc2, dup2(-kFiltK1), mul2(make_float2(B.z, B.w), dup2(-kFiltK2)));
-        const float2 big = add2(oc2, dup2(-0x1p100f));
-        clear[q] = __float_as_uint(big.x) & __float_as_uint(big.y);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float2 t = fma2(ocx, sf[r].vx, fma2(ocy, sf[r].vy, mul2(ocz, sf[r].vz)));
-            const float2 g = fma2(t, t, c);
-            clear[q] &= __float_as_uint(g.x) & __float_as_uint(g.y);
-        }
-    }
-    if (__all_sync(mask, ((clear[0] & clear[1] & clear[2] & clear[3]) >> 31) != 0)) return false;
+                                                        const float* seg, uint32_t (&acc)[kFiltGroup], bool force) {
     // pairs some lane flags, one warp-uniform bit each; one copy of the segment test
-    uint32_t need = 0;
+    uint32_t need = (1u << (kPad / 2)) - 1u;
+    if (!force) {
+        uint32_t clear[kPad / 2];
 #pragma unroll
-    for (int q = 0; q < kPad / 2; ++q) need |= __all_sync(mask, (clear[q] >> 31) != 0) ? 0u : (1u << q);
+        for (int q = 0; q < kPad / 2; ++q) {
+            const float4 A = geo[2 * q], B = geo[2 * q + 1];
+            const float2 ocx = add2(make_float2(A.x, A.y), o2.nox);
+            const float2 ocy = add2(make_float2(A.z, A.w), o2.noy);
+            const float2 ocz = add2(make_float2(B.x, B.y), o2.noz);
+            const float2 oc2 = fma2(ocx, ocx, fma2(ocy, ocy, mul2(ocz, ocz)));
+            // K2 r^2 - K1 |oc|^2 (B.zw = -r^2), and |oc|^2 - 2^100 (positive: too large)
+            const float2 c = fma2(oc2, dup2(-kFiltK1), mul2(make_float2(B.z, B.w), dup2(-kFiltK2)));
+            const float2 big = add2(oc2, dup2(-0x1p100f));
+            clear[q] = __float_as_uint(big.x) & __float_as_uint(big.y);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 t = fma2(ocx, sf[r].vx, fma2(ocy, sf[r].vy, mul2(ocz, sf[r].vz)));
+                const float2 g = fma2(t, t, c);
+                clear[q] &= __float_as_uint(g.x) & __float_as_uint(g.y);
+            }
+        }
+        if (__all_sync(mask, ((clear[0] & clear[1] & clear[2] & clear[3]) >> 31) != 0)) return false;
+        need = 0;
+#pragma unroll
+        for (int q = 0; q < kPad / 2; ++q) need |= __all_sync(mask, (clear[q] >> 31) != 0) ? 0u : (1u << q);
+    }
 #pragma unroll 1
     while (need) {
         const int q = __ffs(need) - 1;
@@ -787,30 +788,21 @@ __device__ __noinline__ uint32_t occluded_filtered(const float4* __restrict__ ge
                                 dup2(seg[(9 * r + 8) * kSegStride])}
                       : SegFilt{dup2(0.f), dup2(0.f), dup2(0.f)};
     }
-    if (exact_only) {  // the filter's bound does not hold for some lane: the segment test throughout
+    // exact_only (the filter's bound does not hold for some lane): the segment test
+    // for every pair of every block
+    if (exact_only) cone = nullptr;
+    const int nb = n / kPad;
+    bool stop = false;
 #pragma unroll 1
-        for (int i0 = 0; i0 < n; i0 += kPad) {
+    for (int w0 = 0; w0 < nb && !stop; w0 += 32) {
+        uint32_t m = cone ? cone[w0 >> 5] : (nb - w0 >= 32 ? 0xffffffffu : (1u << (nb - w0)) - 1u);
 #pragma unroll 1
-            for (int q = 0; q < kPad / 2; ++q) pair_exact<R>(geo + i0, q, o2, seg, acc);
-            bool done = true;
-#pragma unroll
-            for (int r = 0; r < R; ++r) done = done && (acc[r] >> 31);
-            if (__all_sync(mask, done)) break;
-        }
-    } else {
-        const int nb = n / kPad;
-        bool stop = false;
-#pragma unroll 1
-        for (int w0 = 0; w0 < nb && !stop; w0 += 32) {
-            uint32_t m = cone ? cone[w0 >> 5] : (nb - w0 >= 32 ? 0xffffffffu : (1u << (nb - w0)) - 1u);
-#pragma unroll 1
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1u;
-                if (occluded_block_filtered<R>(geo + (size_t)(w0 + b) * kPad, mask, o2, sf, seg, acc)) {
-                    stop = true;
-                    break;
-                }
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            if (occluded_block_filtered<R>(geo + (size_t)(w0 + b) * kPad, mask, o2, sf, seg, acc, exact_only)) {
+                stop = true;
+                break;
             }
         }
     }
