@@ -501,6 +501,14 @@ def extras(args, dev, stream):
         ms = _time_device(lambda: rt.render(ds, w.camera, w.params, out=o, pitch=pitch, launch=launch,
                                             stream=stream, workspace=wsb), stream, 20)
         rec = {"workload": w.name, "frames_per_s": 1e3 / ms, "ms_per_frame": ms, "launch": launch}
+        # executed FP32 work of the same kernels (ncu record of the current sources)
+        ex = recorded_executed(w.name, "rt_render_ws" if launch.get("queued") else "rt_fwd_kernel")
+        if ex:
+            rec.update({"executed_tflops": ex["fp32_flop"] / (ms / 1e3) / 1e12,
+                        "executed_frac": ex["fp32_flop"] / (ms / 1e3) / 1e12 / peak,
+                        "executed_gflop_per_frame": ex["fp32_flop"] / 1e9,
+                        "fma_pipe_busy_pct": ex["fma_pipe_pct"], "issue_active_pct": ex["issue_active_pct"],
+                        "warp_exec_eff": ex["lanes_per_inst"] / 32.0})
         if not args.no_cpu_baseline:
             # algorithmic work from the oracle's counters on a bounded lattice sample
             cs = oracle_sample(w, min(3.0, args.cpu_budget))
