@@ -285,7 +285,8 @@ def test_lean_kernels_follow_the_light_kinds():
     while the host knows the scene has no spherical light.  A scene that gains one by
     a host-side update, or by a device-side update (the light kinds are unknown from
     then on), renders exactly as a fresh upload of it does, in one pass and queued,
-    and matches the oracle on a lattice of pixels."""
+    and matches the oracle on a lattice of pixels; a host-side update that takes the
+    light away again renders as the scene did before."""
     base = S.random_scene(11, 256, 3, 4.0)
     p = S._params(base, width=160, height=96, max_depth=3, shadow_samples=16, out_format=S.OUT_F32, seed=11)
     cam = S.default_camera(4.0)
@@ -308,6 +309,9 @@ def test_lean_kernels_follow_the_light_kinds():
     assert not np.array_equal(before[0], want[0])  # the light's change shows
     plain.update(lit)
     for a, b in zip(frames(plain), want):
+        assert np.array_equal(a, b)
+    plain.update(base)  # the light kinds follow the host description back
+    for a, b in zip(frames(plain), before):
         assert np.array_equal(a, b)
     plain.close()
     dev = rt.DeviceScene(base)
