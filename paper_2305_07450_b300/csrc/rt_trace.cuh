@@ -158,8 +158,8 @@ __device__ __forceinline__ void closest_block_compact(const float4* __restrict__
 // One block of kPad spheres (kPad / 2 pairs at geo[0..kPad)); base = index of its first sphere.
 // COMPACT: the roots of the flagged spheres through one copy of the code (the
 // line-filter kernels, whose code outgrows the instruction cache: 4K frame 3.80 ->
-// 3.61 ms); otherwise unrolled per sphere (the segment-test kernels: 1080p 0.272 ->
-// 0.267 ms against the compact form).  Both give the same bits.
+// 3.61 ms); otherwise unrolled per sphere (the segment-test kernels: 1080p 0.267 ms
+// against 0.272 with the compact form).  Both give the same bits.
 template <bool COMPACT>
 __device__ __forceinline__ void closest_block(const float4* __restrict__ geo, int base, const RayCross& r, float& tb,
                                               int& best) {
@@ -1454,7 +1454,7 @@ constexpr int kShadeAuto = 2;
 // FM bit 2: the scene has no sky and no spherical light, so the kernels are compiled
 // without the sky lookup and the spherical-light sample geometry -- code such a frame
 // never runs, but whose instructions would share the instruction cache with the hot
-// loops (4K frame 4.05 -> 3.96 ms, images bit-identical).
+// loops (4K frame 4.07 -> 3.92 ms, images bit-identical).
 constexpr int kFmLean = 4;
 __host__ __device__ constexpr int fm_path(int fm) { return fm & 3; }
 __host__ __device__ constexpr bool fm_lean(int fm) { return (fm & kFmLean) != 0; }
