@@ -8,7 +8,11 @@ beyond it exempt (oracle margin below 1e-5 x scene scale, or an FP32 sensitivity
 of half an LSB or more).  F32: every channel within 1e-4 or exempt, with the
 plain, margin-exempt and sensitivity-exempt counts reported and the exempt share
 bounded.  The oracle renders the frame once (about 15 s on 16 host cores); both
-tests share it."""
+tests share it.
+
+The 1280x720 and 1920x1080 workloads (RGBA8, the same acceptance level) and the
+1280x720 and 512x512 differentiable workloads in FP32 are compared every pixel too,
+each through the launch the shipped table picks for it."""
 import copy
 
 import numpy as np
@@ -65,5 +69,50 @@ def test_4k_full_frame_f32_queued(workload_4k, reference_4k):
     assert np.all(img[..., 3] == 1.0)
     ok, st = compare_f32(img[..., :3].reshape(-1, 3), ref, margin, sens, workload_4k.scene.scene_scale)
     print(st)
+    assert st["failing"] == 0, st
+    assert st["exempt_share"] <= EXEMPT_SHARE_MAX, st
+
+
+def render_tuned(w, fmt):
+    """A frame through the autotuned launch of its workload (one-pass or queued, as
+    the shipped launch table chooses), output format fmt."""
+    ds = rt.DeviceScene(w.scene)
+    launch = autotune.tune_render(ds, w.scene, w.camera, w.params)
+    p = copy.copy(w.params)
+    p.out_format = fmt
+    ws = rt.alloc_workspace(ds, p) if launch.get("queued") else None
+    out, pitch = rt.alloc_output(p)
+    img = rt.render(ds, w.camera, p, out=out, pitch=pitch, launch=launch, workspace=ws)
+    torch.cuda.synchronize()
+    assert rt.device_errors() == 0
+    res = img.cpu().numpy()
+    ds.close()
+    return res
+
+
+@pytest.mark.parametrize("name", ["720p", "1080p"])
+def test_64_sphere_frames_full_rgba8(name):
+    """Every pixel of the 1280x720 and 1920x1080 workloads (64 spheres + plane, 2
+    point lights, bounce limit 4), RGBA8, at the acceptance level of the 4K frame."""
+    w = S.WORKLOADS[name]()
+    ref, margin, sens = oracle_reference(w)
+    img = render_tuned(w, S.OUT_RGBA8)
+    ok, st = compare_rgba8(img.reshape(-1), ref, margin, sens, w.scene.scene_scale)
+    print(name, st)
+    assert st["pixels"] == w.params.width * w.params.height
+    assert st["failing"] == 0, st
+    assert st["frac_within_1lsb"] >= 0.9999, st
+
+
+@pytest.mark.parametrize("name", ["720p", "diff512"])
+def test_full_frames_f32(name):
+    """Every pixel of the 1280x720 workload and of the 512x512 differentiable one in
+    FP32: every channel within 1e-4 or exempt, the exempt share bounded."""
+    w = S.WORKLOADS[name]()
+    ref, margin, sens = oracle_reference(w)
+    img = render_tuned(w, S.OUT_F32)
+    assert np.all(img[..., 3] == 1.0)
+    ok, st = compare_f32(img[..., :3].reshape(-1, 3), ref, margin, sens, w.scene.scene_scale)
+    print(name, st)
     assert st["failing"] == 0, st
     assert st["exempt_share"] <= EXEMPT_SHARE_MAX, st
