@@ -95,3 +95,27 @@ def test_bounce_queues_rgba8_and_deep_mirrors():
         assert np.array_equal(a, g.cpu().numpy()), (i, ws[i].name)
     assert rt.device_errors() == 0
     b.close()
+
+
+def test_batch_64_scenes_every_pixel_against_oracle():
+    """The 64-scene batch through one graph launch (the bench's batched path): every
+    pixel of every frame in FP32 within 1e-4 of the oracle or exempt, the exempt share
+    of the batch bounded as for the 4K frame."""
+    from parity import EXEMPT_SHARE_MAX
+    ws = S.batch_scenes()
+    dss = [rt.DeviceScene(w.scene) for w in ws]
+    b = rt.Batch(dss, [w.camera for w in ws], [w.params for w in ws])
+    b.launch()
+    torch.cuda.synchronize()
+    assert rt.device_errors() == 0
+    got = [o.cpu().numpy() for o in b.outputs()]
+    b.close()
+    pixels = exempt = 0
+    for w, img in zip(ws, got):
+        ref, margin, sens = oracle_reference(w)
+        ok, st = compare_f32(img[..., :3].reshape(-1, 3), ref, margin, sens, w.scene.scene_scale)
+        assert st["failing"] == 0, (w.name, st)
+        pixels += st["pixels"]
+        exempt += st["pixels"] - st["plain"]
+    print(f"batch: {pixels} pixels, {exempt} exempt")
+    assert exempt <= EXEMPT_SHARE_MAX * pixels
