@@ -1,6 +1,6 @@
 """Batched persistent render (rt_render_batch, rt_batch_* CUDA graph): output
 bit-identical to per-frame rt_render, replays identical, parity with the oracle on
-a small batch."""
+a small batch and on every pixel of the 64-scene batch."""
 import numpy as np
 import pytest
 import torch
