@@ -116,7 +116,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_kernel(const SceneView sv, cons
     StagedScene sc{hdr, CH ? nullptr : tab, sv.geo, CH ? tab + (size_t)warp * kChunk : nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (fm_path(FM) == 1 && !CH) staged_cone(tab, hdr->ns_pad, sc);
+    if constexpr (!CH && (fm_path(FM) == 1 || fm_skip(FM))) staged_cone(tab, hdr->ns_pad, sc);
 
     const int wpr = block_x >> 3;
     const int x = fr.rx0 + blockIdx.x * block_x + (warp % wpr) * 8 + (lane & 7);
@@ -172,7 +172,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_p0_kernel(const SceneView sv, c
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (fm_path(FM) == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
+    if constexpr (fm_path(FM) == 1 || fm_skip(FM)) staged_cone(sc.geo, hdr->ns_pad, sc);
     WsCtl* ctl = reinterpret_cast<WsCtl*>(ws);
     const PathQueue q1 = ws_queue(ws, cap, 1);
     const int wpr = block_x >> 3, wpt = (block_x * block_y) >> 5;
@@ -220,7 +220,7 @@ __global__ void __maxnreg__(fwd_regs(FM)) rt_fwd_queue_kernel(const SceneView sv
     StagedScene sc{hdr, reinterpret_cast<const float4*>(smem + sizeof(SceneHdr)), sv.geo, nullptr, sv.mat, sv.mat2};
     sc.sky = sv.sky;
     sc.flower = sunflower_table(reinterpret_cast<float4*>(smem + flower_off), flower_n, fr.nsamp);
-    if constexpr (fm_path(FM) == 1) staged_cone(sc.geo, hdr->ns_pad, sc);
+    if constexpr (fm_path(FM) == 1 || fm_skip(FM)) staged_cone(sc.geo, hdr->ns_pad, sc);
     const PathQueue cur = ws_queue(ws, cap, k);
     const PathQueue nxt = ws_queue(ws, cap, k + 1);
     if constexpr (fm_path(FM) == 1) {
@@ -1142,6 +1142,8 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
     const int flower_n = s->any_sphere_light && p->shadow_samples >= 16 ? p->shadow_samples : 0;
     // no sky and, as far as the host knows, no spherical light: the lean kernels
     const bool lean = !s->sky_dev && s->kinds_known && !s->any_sphere_light;
+    // sampled lights of several rays possible: the segment-test kernels with light_clear
+    const bool sampled = p->shadow_samples > 1 && (!s->kinds_known || s->any_area || s->any_sphere_light);
     const bool chunked = use_tiled_loop(L, s->ns_pad, (size_t)flower_n * 16);
     const uint32_t flower_off = (uint32_t)((stage_smem_bytes(chunked, s->ns_pad, nwarps) + 15) / 16 * 16);
     const size_t smem = flower_off + (size_t)flower_n * 16;
@@ -1178,10 +1180,12 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         if (hr) {
             if (filt && lean) RT_WS_LAUNCH(true, 1 | kFmLean);
             else if (filt) RT_WS_LAUNCH(true, 1);
+            else if (sampled) RT_WS_LAUNCH(true, kFmSkip);
             else RT_WS_LAUNCH(true, 0);
         } else {
             if (filt && lean) RT_WS_LAUNCH(false, 1 | kFmLean);
             else if (filt) RT_WS_LAUNCH(false, 1);
+            else if (sampled) RT_WS_LAUNCH(false, kFmSkip);
             else RT_WS_LAUNCH(false, 0);
         }
 #undef RT_WS_LAUNCH
@@ -1200,11 +1204,13 @@ static rt_status render_region(const rt_scene* s, const rt_camera* cam, const rt
         if (chunked) RT_FWD_LAUNCH(true, true, 0);
         else if (filt && lean) RT_FWD_LAUNCH(true, false, 1 | kFmLean);
         else if (filt) RT_FWD_LAUNCH(true, false, 1);
+        else if (sampled) RT_FWD_LAUNCH(true, false, kFmSkip);
         else RT_FWD_LAUNCH(true, false, 0);
     } else {
         if (chunked) RT_FWD_LAUNCH(false, true, 0);
         else if (filt && lean) RT_FWD_LAUNCH(false, false, 1 | kFmLean);
         else if (filt) RT_FWD_LAUNCH(false, false, 1);
+        else if (sampled) RT_FWD_LAUNCH(false, false, kFmSkip);
         else RT_FWD_LAUNCH(false, false, 0);
     }
 #undef RT_FWD_LAUNCH

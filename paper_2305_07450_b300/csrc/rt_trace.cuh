@@ -957,45 +957,136 @@ __device__ __forceinline__ int rays_of_light(const Frame& fr, float4 Ls) {
     return (Ls.x > 0.0f || Ls.y > 0.0f) ? fr.nsamp : 1;
 }
 
-template <bool HITREC, bool CH, bool ACC = false>
+// A sampled light (nr > 1 rays) whose every segment from this shading point is
+// certainly unblocked: the cone of its sample region seen from p (the one-lane path's
+// cone pre-pass: axis to the centre, kappa below the cosine to the square's corners or
+// the sphere's tangent cone, less 2^-17) clears every block of the staged table, by
+// cone_block_clear with apex po, and the plane cannot block either (the one-lane
+// path's skip, same bounds).  Each segment would test unblocked, so vis = n / n = 1.
+// Needs the cone bound of the staged table (sc.cone_r2 > 0).
+__device__ __forceinline__ bool light_clear(const StagedScene& sc, const SceneHdr& h, int l, f3 p, f3 p_lo, f3 po) {
+    const float4 Lp = h.light_p[l], Ls = h.light_s[l];
+    const f3 Lv = sub(sub(xyz(Lp), p), p_lo);
+    const float ri = rsqrtf(dot(Lv, Lv));
+    const f3 ax = scl(Lv, ri);
+    float kap;
+    if (Ls.x > 0.0f) {
+        const float hs = 0.5f * Ls.x;
+        kap = 1.0f;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            const f3 cv = add(Lv, mk3((c & 1) ? hs : -hs, 0.0f, (c & 2) ? hs : -hs));
+            kap = fminf(kap, dot(ax, cv) * rsqrtf(dot(cv, cv)));
+        }
+    } else {
+        const float sr = Ls.y * ri * (1.0f + 0x1p-20f);  // >= R / dist
+        kap = sqrt_bound(fmaxf(fmaf(-sr, sr, 1.0f), 0.0f));
+    }
+    kap -= 0x1p-17f;
+    if (!(kap >= 0.5f)) return false;  // NaN: not clear
+    const float sg = sqrt_bound(fmaxf(fmaf(-kap, kap, 1.0f), 0.0f)) * (1.0f + 0x1p-18f);  // >= sin alpha
+    const float2 nc0 = dup2(-fmaf(kap, kap, -0x1p-16f)), tw = dup2(2.0f * sqrt_bound(sc.cone_r2) * sg);
+    const float2 r2 = dup2(sc.cone_r2);
+    const RayPair o2 = ray_pair(po);
+    const float2 axx = dup2(ax.x), axy = dup2(ax.y), axz = dup2(ax.z);
+#pragma unroll 1
+    for (int i0 = 0; i0 < h.ns_pad; i0 += kPad)
+        if (!cone_block_clear(sc.geo + i0, o2, axx, axy, axz, nc0, tw, r2)) return false;
+    if (!h.has_plane) return true;
+    const f3 pn = xyz(h.plane_g);
+    const float num = -(dot(po, pn) + h.plane_g.w);
+    if (num == 0.0f) return true;
+    if (num > 0.0f) return false;
+    const float an = fabsf(pn.x) + fabsf(pn.y) + fabsf(pn.z);
+    const float ext = Ls.x > 0.0f ? 0.5f * Ls.x * (fabsf(pn.x) + fabsf(pn.z)) : Ls.y * an;
+    const float lo = dot(xyz(Lp), pn) - ext - (dot(p, pn) + dot(p_lo, pn));
+    const float sc_ = (fmaxf(fabsf(Lp.x), fmaxf(fabsf(Lp.y), fabsf(Lp.z))) + Ls.x + Ls.y +
+                       fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))) + 1.0f) * an;
+    return lo > 0x1p-14f * sc_;  // NaN: false
+}
+
+template <bool HITREC, bool CH, bool ACC = false, bool SKIP = false>
 __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, f3 p,
                                               f3 p_lo, f3 n, f3 po, f3 d, float ks, float e, float* __restrict__ hr,
                                               size_t hr_k, size_t hr_plane) {
     const SceneHdr& h = *sc.hdr;
     HitShade out{fr.ka, 0.0f};
-    // lights on the lit side and the number of shadow rays they need
-    uint32_t lit = 0;
+    // lights on the lit side and the number of shadow rays they need; sampled lights
+    // that light_clear proves unblocked take no rays (vis = 1)
+    uint32_t lit = 0, clear = 0;
     int total = 0;
 #pragma unroll 1
     for (int li = 0; li < h.nl; ++li) {
         const f3 lh = normalize(sub(sub(xyz(h.light_p[li]), p), p_lo));
         if (dot(n, lh) > 0.0f) {
             lit |= 1u << li;
-            total += rays_of_light(fr, h.light_s[li]);
+            const int nr = rays_of_light(fr, h.light_s[li]);
+            bool skip = false;
+            if constexpr (!CH && !ACC && SKIP) skip = nr > 1 && sc.cone_r2 > 0.0f && light_clear(sc, h, li, p, p_lo, po);
+            if (skip) clear |= 1u << li;
+            else total += nr;
         }
         if (HITREC) hr[hr_k + (size_t)(2 + li) * hr_plane] = 0.0f;
     }
-    // cursor (cl, cs): light and sample of this lane's next ray to attribute
-    int cl = lit ? __ffs(lit) - 1 : 0, cs = 0, cnt = 0;
+    const uint32_t traced = lit & ~clear;
+    // rem: the lit lights not attributed yet; (cs, cnt): results of its first so far
+    uint32_t rem = lit;
+    int cs = 0, cnt = 0;
+    // (l, s): light and sample of the next segment to set up
+    int l = traced ? __ffs(traced) - 1 : 0, s = 0;
     uint4 w = make_uint4(0, 0, 0, 0);
-    int done = 0;
+    int done = 0, kp = 0;  // segments set up so far; results of the previous group
+    uint32_t bp = 0;       // their blocked bits
     const unsigned mask = __activemask();
 #pragma unroll 1
     while (true) {
+        // attribute in light order: the previous group's results as each light's
+        // segments complete, a cleared light (vis = 1) in its turn
+        int j = 0;
+#pragma unroll 1
+        while (rem) {
+            const int cl = __ffs(rem) - 1;
+            const float4 Lp = h.light_p[cl];
+            float vis = 1.0f;
+            if (!((clear >> cl) & 1u)) {
+                const int nr = rays_of_light(fr, h.light_s[cl]);
+                bool ready = false;
+#pragma unroll 1
+                while (j < kp) {
+                    cnt += (bp >> j) & 1u ? 0 : 1;
+                    ++j;
+                    if (++cs == nr) {
+                        ready = true;
+                        break;
+                    }
+                }
+                if (!ready) break;
+                vis = (float)cnt / (float)nr;
+                cs = 0;
+                cnt = 0;
+            }
+            const f3 lh = normalize(sub(sub(xyz(Lp), p), p_lo));
+            const float ndl = dot(n, lh);
+            const float sp = light_spec(fr, n, d, lh, ndl, e);
+            const float iv = Lp.w * vis;
+            out.A = fmaf(iv, ndl, out.A);
+            out.S = fmaf(iv * ks, sp, out.S);
+            if (HITREC) hr[hr_k + (size_t)(2 + cl) * hr_plane] = vis;
+            rem &= rem - 1u;
+        }
         const int kr = min(kShadowGroup, total - done);
         const int R = (int)__reduce_max_sync(mask, (unsigned)kr);
         if (R == 0) break;
         f3 sw[kShadowGroup], snv[kShadowGroup];  // W and -V of each segment
         bool occ[kShadowGroup];
-        int l = cl, s = cs;
         LightFrame lf{};  // of spherical light lf_l
         int lf_l = -1;
 #pragma unroll
-        for (int j = 0; j < kShadowGroup; ++j) {
-            sw[j] = mk3(0.f, 0.f, 0.f);
-            snv[j] = mk3(0.f, 0.f, 0.f);
-            occ[j] = true;
-            if (j < kr) {
+        for (int jj = 0; jj < kShadowGroup; ++jj) {
+            sw[jj] = mk3(0.f, 0.f, 0.f);
+            snv[jj] = mk3(0.f, 0.f, 0.f);
+            occ[jj] = true;
+            if (jj < kr) {
                 const float4 Lp = h.light_p[l];
                 const float4 Ls = h.light_s[l];
                 const int nr = rays_of_light(fr, Ls);
@@ -1008,12 +1099,12 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
                                  : xyz(Lp);
                 // V = X - p (p as hi + lo), W = V / |V|^2
                 const f3 V = sub(sub(X, p), p_lo);
-                sw[j] = scl(V, rcp_approx(dot(V, V)));
-                snv[j] = scl(V, -1.0f);
-                occ[j] = false;
+                sw[jj] = scl(V, rcp_approx(dot(V, V)));
+                snv[jj] = scl(V, -1.0f);
+                occ[jj] = false;
                 if (++s == nr) {
                     s = 0;
-                    const uint32_t rest = lit & ~((2u << l) - 1u);
+                    const uint32_t rest = traced & ~((2u << l) - 1u);
                     l = rest ? __ffs(rest) - 1 : 0;
                 }
             }
@@ -1027,29 +1118,10 @@ __device__ __forceinline__ HitShade shade_hit(const StagedScene& sc, const Frame
         } else {
             occluded_group<(kShadowGroup < 4 ? 1 : 4), CH, ACC>(sc, po, sw, snv, occ);
         }
-        // attribute the results to their lights in the same order
+        bp = 0;
 #pragma unroll
-        for (int j = 0; j < kShadowGroup; ++j) {
-            if (j < kr) {
-                cnt += occ[j] ? 0 : 1;
-                const float4 Lp = h.light_p[cl];
-                const int nr = rays_of_light(fr, h.light_s[cl]);
-                if (++cs == nr) {
-                    const float vis = (float)cnt / (float)nr;
-                    const f3 lh = normalize(sub(sub(xyz(Lp), p), p_lo));
-                    const float ndl = dot(n, lh);
-                    const float sp = light_spec(fr, n, d, lh, ndl, e);
-                    const float iv = Lp.w * vis;
-                    out.A = fmaf(iv, ndl, out.A);
-                    out.S = fmaf(iv * ks, sp, out.S);
-                    if (HITREC) hr[hr_k + (size_t)(2 + cl) * hr_plane] = vis;
-                    cs = 0;
-                    cnt = 0;
-                    const uint32_t rest = lit & ~((2u << cl) - 1u);
-                    cl = rest ? __ffs(rest) - 1 : 0;
-                }
-            }
-        }
+        for (int jj = 0; jj < kShadowGroup; ++jj) bp |= occ[jj] ? (1u << jj) : 0u;
+        kp = kr;
         done += kr;
     }
     return out;
@@ -1456,8 +1528,14 @@ constexpr int kShadeAuto = 2;
 // never runs, but whose instructions would share the instruction cache with the hot
 // loops (4K frame 4.07 -> 3.92 ms, images bit-identical).
 constexpr int kFmLean = 4;
+// FM bit 3 (segment-test path): the scene may hold sampled lights of several rays, so
+// the kernels stage the cone bound and shade_hit tries light_clear on each of them;
+// kernels for scenes without such lights are compiled without that code (720p frame
+// of point lights 0.143 -> 0.139 ms).
+constexpr int kFmSkip = 8;
 __host__ __device__ constexpr int fm_path(int fm) { return fm & 3; }
 __host__ __device__ constexpr bool fm_lean(int fm) { return (fm & kFmLean) != 0; }
+__host__ __device__ constexpr bool fm_skip(int fm) { return (fm & kFmSkip) != 0; }
 
 template <bool HITREC, bool CH, bool ACC, int FM = kShadeAuto, bool IT = false>
 __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& fr, uint32_t pix, int k, int id,
@@ -1476,7 +1554,8 @@ __device__ __forceinline__ void shade_step(const StagedScene& sc, const Frame& f
     if (filt)
         sh = shade_hit_staged<HITREC, IT, fm_lean(FM)>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
     else
-        sh = shade_hit<HITREC, CH, ACC>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k, hr_plane);
+        sh = shade_hit<HITREC, CH, ACC, fm_skip(FM)>(sc, fr, pix, k, p, hg.p_lo, n, po, d, m.w, m2.x, hr, hr_k,
+                                                    hr_plane);
     step_tail(fr, k, m, m2, sh, n, po, po_lo, o, o_lo, d, T, out);
 }
 
