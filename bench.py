@@ -676,8 +676,9 @@ def fwd_adjoint(dev, stream):
     truth = S.perturbed_target(w)
     tgt = inverse.target_image(truth, w)
     # untimed: the first optimizer step of a process imports PyTorch modules lazily
-    # (seconds on a cold box), which is not the loop's cost
-    inverse.inverse_render(w, tgt, steps=2, lr=0.05)
+    # (seconds on a cold box), which is not the loop's cost; with the truth, so that the
+    # error measures at the end are warm as well
+    inverse.inverse_render(w, tgt, steps=2, lr=0.05, truth=truth)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = inverse.inverse_render(w, tgt, steps=200, lr=0.05, truth=truth)
